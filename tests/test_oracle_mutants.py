@@ -1,0 +1,28 @@
+"""Plant plausible mistakes in copies of the oracle (built on the CPU with a
+mutation define) and check that the pin suite rejects every one of them:
+    1  g(j+k) instead of g(j-k) in Eq. 1
+    2  w^(-ut) instead of w^(ut) in Eq. 2
+    3  the 1/N of Eq. 3 dropped
+    4  w^(ut) instead of w^(-ut) in Eq. 3
+    5  the last term of the sum in Eq. 1 dropped
+"""
+import os
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5])
+def test_mutant_is_caught(tmp_path, mutant):
+    so = oracle.build(out=os.path.join(tmp_path, f"mut{mutant}.so"), defines={"ORACLE_MUTANT": mutant})
+    o = oracle.Oracle(oracle.load(so))
+    fast = [P.pin_hand_example, P.pin_impulses, P.pin_roundtrip_linear,
+            P.pin_conv_closed_forms, P.pin_theorem]
+    failed = P.run_pins(o, fast)
+    assert failed, f"mutant {mutant} passed every pin"
+
+
+def test_real_oracle_passes_fast_subset(orc):
+    assert P.run_pins(orc, [P.pin_hand_example, P.pin_impulses]) == []
