@@ -1,0 +1,200 @@
+/*
+ * ntt_gb300.h -- C ABI of the GB300 (sm_103a) exact digital circular
+ * convolution library.
+ *
+ * The library computes, exactly and modulo a prime m, the circular
+ * convolution of two integer sequences of a power-of-two length N
+ *
+ *     h(j) = < sum_{k=0}^{N-1} f(k) * g(<j-k>_N) >_m           (Eq. 1)
+ *
+ * through the number-theoretic transform whose kernel is a power of two
+ *
+ *     X(u) = < sum_{t=0}^{N-1} x(t) * w^{ut} >_m,  w = 2^(N_Max/N)   (Eq. 2)
+ *     x(t) = < N^-1 sum_{u=0}^{N-1} X(u) * w^{<-ut>_N} >_m            (Eq. 3)
+ *
+ * where N_Max = ord_m(2) is a power of two, i.e. m is a prime factor of a
+ * Fermat number (Sec. III-A, Prop. 2; Table 1 lists 641, 2424833, 319489 and
+ * 13631489, the last allowing every N <= 2^19).  <a>_m is the remainder in
+ * [0, m) (Appendix A) and N^-1 the multiplicative inverse of N mod m.
+ *
+ * Conventions shared by every entry point
+ *   - Words.  Sequences are arrays of unsigned words: uint32_t when
+ *     m < 2^25, uint64_t when 2^25 <= m < 2^57 (ntt_plan_word_bits tells
+ *     which).  Inputs must lie in [0, m); the fast paths do not check this
+ *     and the result for other inputs is unspecified (ntt_check_range checks
+ *     a buffer explicitly).  Every output is canonical, in [0, m).
+ *   - Layout.  A batch of B sequences of length N is one contiguous
+ *     row-major array [B][N]; element t of sequence b is at index b*N + t.
+ *     Spectra (ntt_forward output, ntt_inverse input) are in natural order
+ *     u = 0 .. N-1.
+ *   - Memory.  Every data pointer named *_dev is a device pointer of the
+ *     current CUDA device, owned by the caller, and must stay valid until the
+ *     work queued on `stream` has completed.  Input and output may alias
+ *     (in-place calls are allowed).  Pointers must be aligned to the word
+ *     size.  Plans own their twiddle tables and scratch buffers (device
+ *     memory allocated by ntt_plan, freed by ntt_plan_destroy).
+ *   - Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls enqueue work and return without synchronising, except where a
+ *     comment says otherwise; errors of the launch itself are returned,
+ *     errors of the asynchronous work surface on the stream.
+ *   - Errors.  Every call returns an ntt_status; nothing is thrown across the
+ *     ABI.  ntt_last_error() gives a human-readable message for the last
+ *     failure on the calling thread.
+ */
+#ifndef NTT_GB300_H
+#define NTT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ntt_stream_t;         /* == cudaStream_t */
+typedef struct ntt_plan_s *ntt_plan_t;            /* opaque, owned by the library */
+typedef struct ntt_batch_s *ntt_batch_t;          /* opaque, owned by the library */
+
+typedef enum {
+    NTT_OK = 0,
+    NTT_ERR_LENGTH = 1,    /* N not a power of two, or N does not divide ord_m(2), or N above the supported maximum */
+    NTT_ERR_MODULUS = 2,   /* m not prime, or ord_m(2) not a power of two (m divides no Fermat number) */
+    NTT_ERR_WORD = 3,      /* m too large for the supported word sizes (m >= 2^57) */
+    NTT_ERR_RANGE = 4,     /* an input word is >= m (ntt_check_range only) */
+    NTT_ERR_OOM = 5,       /* device or host allocation failed */
+    NTT_ERR_CUDA = 6,      /* a CUDA runtime call failed; see ntt_last_error() */
+    NTT_ERR_TIMEOUT = 7,   /* a bounded device-side wait expired */
+    NTT_ERR_ARG = 8,       /* null pointer, zero count or otherwise invalid argument */
+    NTT_ERR_ADMISSION = 9  /* a request does not fit the serving memory budget */
+} ntt_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *ntt_status_str(ntt_status s);
+
+/* Message describing the last failure on the calling thread (static per
+ * thread, overwritten by the next failure; "" if none). */
+const char *ntt_last_error(void);
+
+/* ------------------------------------------------------------------ plans */
+
+/* Create a plan for length N modulo m (Eq. 2/3 with w = 2^(ord_m(2)/N),
+ * Sec. I; multiplicative inverse of N by extended Euclid, Appendix A).
+ * Validates that m is prime and that ord_m(2) is a power of two (Prop. 2),
+ * and that N is a power of two dividing ord_m(2) (Sec. I).  Supported
+ * lengths: 1 <= N <= 2^19 for 32-bit words, 1 <= N <= 2^18 for 64-bit
+ * words.  Builds the twiddle table {2^e mod m} on the host by doubling and
+ * uploads it once to the current device; it stays resident.  Synchronous.
+ * Errors: NTT_ERR_MODULUS, NTT_ERR_LENGTH, NTT_ERR_WORD, NTT_ERR_OOM,
+ * NTT_ERR_CUDA, NTT_ERR_ARG (out == NULL). */
+ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out);
+
+/* Release a plan and its device memory.  The caller must ensure no queued
+ * work still uses it.  NULL is ignored. */
+void ntt_plan_destroy(ntt_plan_t plan);
+
+typedef struct {
+    uint64_t m;          /* modulus */
+    uint32_t N;          /* transform length */
+    uint32_t log2N;
+    uint64_t n_max;      /* ord_m(2) */
+    uint64_t omega;      /* w = 2^(n_max/N) mod m */
+    uint64_t n_inv;      /* N^-1 mod m */
+    uint32_t word_bits;  /* 32 or 64 */
+    uint32_t four_step;  /* 1 when N exceeds one thread block and the split path is used */
+    uint32_t wave;       /* pairs per scratch wave of the split path (0 if unused) */
+    uint32_t reserved;
+} ntt_plan_info_t;
+
+/* Fill *info with the plan's parameters.  Errors: NTT_ERR_ARG. */
+ntt_status ntt_plan_get_info(ntt_plan_t plan, ntt_plan_info_t *info);
+
+/* 32 or 64 (the word type of every buffer used with this plan); 0 if plan is NULL. */
+int ntt_plan_word_bits(ntt_plan_t plan);
+
+/* ------------------------------------------------------------ transforms */
+
+/* Forward transform of Eq. 2 on `batch` sequences: X_dev[b][u] =
+ * < sum_t x_dev[b][t] * w^{ut} >_m, natural order.  Errors: NTT_ERR_ARG
+ * (NULL pointer or batch == 0), NTT_ERR_CUDA. */
+ntt_status ntt_forward(ntt_plan_t plan, const void *x_dev, void *X_dev, size_t batch, ntt_stream_t stream);
+
+/* Inverse transform of Eq. 3 including the factor N^-1: x_dev[b][t] =
+ * < N^-1 sum_u X_dev[b][u] * w^{<-ut>_N} >_m.  Errors as ntt_forward. */
+ntt_status ntt_inverse(ntt_plan_t plan, const void *X_dev, void *x_dev, size_t batch, ntt_stream_t stream);
+
+/* ---------------------------------------------------------- convolutions */
+
+/* Circular convolution (Eq. 1) of `batch` pairs by the convolution theorem:
+ * forward transforms of f and g, pointwise product <F(u) G(u)>_m, inverse
+ * transform with N^-1 (Sec. I), fused on the device.  h_dev may alias f_dev
+ * or g_dev.  Lengths above one thread block use the plan's scratch in waves.
+ * Errors: NTT_ERR_ARG, NTT_ERR_CUDA. */
+ntt_status conv_circular(ntt_plan_t plan, const void *f_dev, const void *g_dev, void *h_dev,
+                         size_t batch, ntt_stream_t stream);
+
+/* The same result computed in the plain form, one kernel launch per
+ * butterfly stage over the whole batch (2 log2 N + 2 launches), with every
+ * stage reading and writing device memory.  Kept as the comparison baseline
+ * for the fused form.  work_dev must hold 2 * batch * N words of scratch
+ * (caller-owned).  Errors: NTT_ERR_ARG, NTT_ERR_CUDA. */
+ntt_status conv_circular_plain(ntt_plan_t plan, const void *f_dev, const void *g_dev, void *h_dev,
+                               size_t batch, void *work_dev, ntt_stream_t stream);
+
+/* conv_circular with the inputs and output in HOST memory: the library
+ * copies f and g to the device, convolves, and copies h back, in chunks on
+ * `stream` so that the copies of one chunk overlap the convolution of the
+ * next.  Host buffers should be page-locked (cudaHostAlloc) for full copy
+ * speed.  Allocates device staging memory on first use (kept by the plan).
+ * Returns after h_host is complete (synchronises `stream`).
+ * Errors: NTT_ERR_ARG, NTT_ERR_OOM, NTT_ERR_CUDA. */
+ntt_status conv_circular_host(ntt_plan_t plan, const void *f_host, const void *g_host, void *h_host,
+                              size_t batch, ntt_stream_t stream);
+
+/* One convolution of an uneven batch: sequences f, g, h of length N (device
+ * pointers, caller-owned). */
+typedef struct {
+    const void *f;
+    const void *g;
+    void *h;
+    uint32_t N;
+    uint32_t reserved;
+} ntt_conv_desc;
+
+/* Convolve `count` independent pairs of (possibly) different power-of-two
+ * lengths modulo one prime m.  Equivalent to ntt_batch_plan + ntt_batch_exec
+ * + ntt_batch_destroy, with the batch plan cached by the library for the
+ * last (m, descriptor list) seen on this thread.  Errors as ntt_plan and
+ * conv_circular. */
+ntt_status conv_batched(uint64_t m, const ntt_conv_desc *descs, size_t count, ntt_stream_t stream);
+
+/* Build a reusable execution plan for an uneven batch: groups the
+ * descriptors by length, builds the per-length plans and device work lists,
+ * picks each length's schedule (from the autotune table when one is loaded),
+ * and allocates the scratch it needs.  Synchronous.  The descriptor array is
+ * copied; the pointers it holds must stay valid while the batch plan is
+ * executed. */
+ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, size_t count, ntt_batch_t *out);
+
+/* Enqueue every convolution of the batch plan on `stream` (length classes
+ * run on forked internal streams joined back into `stream`).  Capturable in
+ * a CUDA graph. */
+ntt_status ntt_batch_exec(ntt_batch_t batch, ntt_stream_t stream);
+
+/* Capture ntt_batch_exec into a CUDA graph once (first call) and replay it on
+ * `stream` (every call). */
+ntt_status ntt_batch_exec_graph(ntt_batch_t batch, ntt_stream_t stream);
+
+void ntt_batch_destroy(ntt_batch_t batch);
+
+/* ----------------------------------------------------------------- checks */
+
+/* Count the words of `count` words at data_dev (word size of the plan) that
+ * are >= m; returns NTT_ERR_RANGE if any, NTT_OK otherwise.  Synchronous.
+ * *bad (optional) receives the count. */
+ntt_status ntt_check_range(ntt_plan_t plan, const void *data_dev, size_t count, uint64_t *bad, ntt_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTT_GB300_H */

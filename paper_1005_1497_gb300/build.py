@@ -1,0 +1,83 @@
+"""Build step of the CUDA library: compiles csrc/*.cu for sm_103a with nvcc in
+parallel and links ``libntt_gb300.so`` next to this file (in-tree)."""
+from __future__ import annotations
+
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+ROOT = os.path.dirname(HERE)
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(HERE, "libntt_gb300.so")
+BUILD = os.path.join(ROOT, "_build")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
+
+
+def _sources():
+    return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def _headers_digest() -> str:
+    h = hashlib.sha256()
+    for d in (CSRC, INCLUDE):
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".h", ".cuh")):
+                with open(os.path.join(d, f), "rb") as fh:
+                    h.update(f.encode() + fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    """Compile every CUDA source (objects cached per source and header digest)
+    and link the shared library.  Returns its path."""
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    digest = _headers_digest()
+    objs, todo = [], []
+    for src in _sources():
+        path = os.path.join(CSRC, src)
+        with open(path, "rb") as fh:
+            tag = hashlib.sha256(fh.read() + digest.encode()).hexdigest()[:16]
+        obj = os.path.join(BUILD, f"{src[:-3]}.{tag}.o")
+        objs.append(obj)
+        if force or not os.path.exists(obj):
+            todo.append((path, obj))
+
+    def compile_one(item):
+        path, obj = item
+        cmd = [nvcc, *ARCH, *FLAGS, "-c", path, "-o", obj + ".tmp"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {os.path.basename(path)}:\n{res.stderr}")
+        os.replace(obj + ".tmp", obj)
+        if verbose:
+            print("compiled", os.path.basename(path), file=sys.stderr)
+
+    if todo:
+        with ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
+            list(ex.map(compile_one, todo))
+    if todo or force or not os.path.exists(LIB):
+        tmp = LIB + ".tmp"
+        res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stderr}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,253 @@
+// launch_impl.cuh -- template bodies of the launchers (included by the
+// per-word-type translation units only).
+#pragma once
+
+#include "ntt_launch.h"
+
+namespace ntt {
+
+template <typename K>
+static cudaError_t ensure_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename W>
+int Launch<W>::rows_per_block(int LR)
+{
+    const int RB = Arith<W>::RB;
+    const int RL = LR < RB ? LR : RB;
+    return BLOCK >> (LR - RL);
+}
+
+template <typename W, int L, int SRC>
+static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+    if constexpr (L <= LRMax<W>::v) {
+        constexpr size_t smem = RowShape<W, L, L>::smem(2);
+        static const cudaError_t init = ensure_smem(k_conv_rows<W, L, L, SRC>, smem);
+        if (init != cudaSuccess) return init;
+        k_conv_rows<W, L, L, SRC><<<grid, BLOCK, smem, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W, int L>
+static cudaError_t launch_conv_split(const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+    constexpr int LR = LRMax<W>::v;
+    if constexpr (L > LR && L <= LR + 5) {
+        constexpr size_t smem = RowShape<W, L, LR>::smem(2);
+        static const cudaError_t init = ensure_smem(k_conv_rows<W, L, LR, 0>, smem);
+        if (init != cudaSuccess) return init;
+        k_conv_rows<W, L, LR, 0><<<grid, BLOCK, smem, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W, int L>
+static cudaError_t launch_rows_fwd(const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+    constexpr int LR = LRMax<W>::v;
+    if constexpr (L > LR && L <= LR + 5) {
+        constexpr size_t smem = RowShape<W, L, LR>::smem(1);
+        static const cudaError_t init = ensure_smem(k_rows_fwd<W, L, LR>, smem);
+        if (init != cudaSuccess) return init;
+        k_rows_fwd<W, L, LR><<<grid, BLOCK, smem, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W, int L, int NS, int SRC>
+static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
+{
+    constexpr int LR = LRMax<W>::v;
+    if constexpr (L > LR && L <= LR + 5) {
+        const long long threads = a.npairs << LR;
+        const int blocks = (int)((threads + 255) / 256);
+        k_cols_fwd<W, L, LR, NS, SRC><<<blocks, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W, int L, int DST>
+static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
+{
+    constexpr int LR = LRMax<W>::v;
+    if constexpr (L > LR && L <= LR + 5) {
+        const long long threads = a.npairs << LR;
+        const int blocks = (int)((threads + 255) / 256);
+        k_cols_inv<W, L, LR, DST><<<blocks, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W, int L, bool INV>
+static cudaError_t launch_ntt_full(const NttArgs<W> &a, int grid, cudaStream_t st)
+{
+    if constexpr (L <= LRMax<W>::v) {
+        constexpr size_t smem = RowShape<W, L, L>::smem(1);
+        static const cudaError_t init = ensure_smem(k_ntt_rows<W, L, INV>, smem);
+        if (init != cudaSuccess) return init;
+        k_ntt_rows<W, L, INV><<<grid, BLOCK, smem, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W, int L, bool INV>
+static cudaError_t launch_bitrev(const W *src, W *dst, long long batch, const ModC<W> &c, cudaStream_t st)
+{
+    if constexpr (L >= 1) {
+        const long long n = batch << L;
+        k_bitrev_out<W, L, INV><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, batch, c);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+#define NTT_SWITCH_L(CALL)                                                               \
+    switch (L) {                                                                         \
+    case 0: return CALL(0); case 1: return CALL(1); case 2: return CALL(2);              \
+    case 3: return CALL(3); case 4: return CALL(4); case 5: return CALL(5);              \
+    case 6: return CALL(6); case 7: return CALL(7); case 8: return CALL(8);              \
+    case 9: return CALL(9); case 10: return CALL(10); case 11: return CALL(11);          \
+    case 12: return CALL(12); case 13: return CALL(13); case 14: return CALL(14);        \
+    case 15: return CALL(15); case 16: return CALL(16); case 17: return CALL(17);        \
+    case 18: return CALL(18); case 19: return CALL(19);                                  \
+    default: return cudaErrorInvalidValue;                                               \
+    }
+
+template <typename W>
+cudaError_t Launch<W>::conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+    if (src == 1) {
+#define C1(X) launch_conv_full<W, X, 1>(a, grid, st)
+        NTT_SWITCH_L(C1)
+#undef C1
+    }
+#define C0(X) launch_conv_full<W, X, 0>(a, grid, st)
+    NTT_SWITCH_L(C0)
+#undef C0
+}
+
+template <typename W>
+cudaError_t Launch<W>::conv_rows_split(int L, const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+#define C(X) launch_conv_split<W, X>(a, grid, st)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W>
+cudaError_t Launch<W>::rows_fwd(int L, const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+#define C(X) launch_rows_fwd<W, X>(a, grid, st)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W>
+cudaError_t Launch<W>::cols_fwd(int L, int ns, int src, const ColArgs<W> &a, cudaStream_t st)
+{
+    if (ns == 2 && src == 0) {
+#define C(X) launch_cols_fwd<W, X, 2, 0>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (ns == 2 && src == 1) {
+#define C(X) launch_cols_fwd<W, X, 2, 1>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (ns == 1 && src == 0) {
+#define C(X) launch_cols_fwd<W, X, 1, 0>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename W>
+cudaError_t Launch<W>::cols_inv(int L, int dst, const ColArgs<W> &a, cudaStream_t st)
+{
+    if (dst == 1) {
+#define C(X) launch_cols_inv<W, X, 1>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    }
+#define C(X) launch_cols_inv<W, X, 0>(a, st)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W>
+cudaError_t Launch<W>::ntt_full(int L, bool inv, const NttArgs<W> &a, int grid, cudaStream_t st)
+{
+    if (inv) {
+#define C(X) launch_ntt_full<W, X, true>(a, grid, st)
+        NTT_SWITCH_L(C)
+#undef C
+    }
+#define C(X) launch_ntt_full<W, X, false>(a, grid, st)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W>
+cudaError_t Launch<W>::bitrev_out(int L, bool inv, const W *src, W *dst, long long batch, const ModC<W> &c,
+                                  cudaStream_t st)
+{
+    if (inv) {
+#define C(X) launch_bitrev<W, X, true>(src, dst, batch, c, st)
+        NTT_SWITCH_L(C)
+#undef C
+    }
+#define C(X) launch_bitrev<W, X, false>(src, dst, batch, c, st)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W>
+cudaError_t Launch<W>::plain(int L, const W *f, const W *g, W *h, W *work, long long batch, const W *tw,
+                             const ModC<W> &c, int grid, cudaStream_t st)
+{
+    const int threads = 256;
+    if (L == 0) {
+        // N = 1: the convolution is the single product
+        cudaError_t e = cudaMemcpyAsync(work, f, sizeof(W) * batch, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(work + batch, g, sizeof(W) * batch, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        for (int d = 0; d < L; ++d) {
+            k_plain_fwd<W><<<grid, threads, 0, st>>>(f, g, work, batch, L, d, tw, c);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    k_plain_pointwise<W><<<grid, threads, 0, st>>>(work, batch, L, c);
+    for (int d = L - 1; d >= 0; --d) k_plain_inv<W><<<grid, threads, 0, st>>>(work, batch, L, d, tw, c);
+    k_plain_final<W><<<grid, threads, 0, st>>>(work, h, batch, L, c);
+    return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t Launch<W>::check_range(const W *data, long long n, W m, unsigned long long *bad, int grid,
+                                   cudaStream_t st)
+{
+    k_check_range<W><<<grid, 256, 0, st>>>(data, n, m, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace ntt

@@ -1,0 +1,6 @@
+// Fused-convolution kernel instantiations for 32-bit words.
+#include "launch_impl.cuh"
+namespace ntt {
+template int Launch<uint32_t>::rows_per_block(int);
+template cudaError_t Launch<uint32_t>::conv_full(int, int, const RowArgs<uint32_t> &, int, cudaStream_t);
+}  // namespace ntt

@@ -1,0 +1,6 @@
+// Fused-convolution kernel instantiations for 64-bit words.
+#include "launch_impl.cuh"
+namespace ntt {
+template int Launch<uint64_t>::rows_per_block(int);
+template cudaError_t Launch<uint64_t>::conv_full(int, int, const RowArgs<uint64_t> &, int, cudaStream_t);
+}  // namespace ntt

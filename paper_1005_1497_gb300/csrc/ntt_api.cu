@@ -1,0 +1,405 @@
+// ntt_api.cu -- C ABI of the library: plans (host number theory, twiddle
+// tables), dispatch of the transforms and convolutions, batch plans and the
+// host-buffer path.  Declared in include/ntt_gb300.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ntt_gb300.h"
+#include "ntt_launch.h"
+#include "nt_host.h"
+#include "ntt_internal.h"
+
+using ntt::ColArgs;
+using ntt::DevDesc;
+using ntt::Launch;
+using ntt::ModC;
+using ntt::NttArgs;
+using ntt::RowArgs;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local char g_last_error[512] = "";
+
+ntt_status ntt_fail(ntt_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+static ntt_status cuda_fail(cudaError_t e, const char *what)
+{
+    return ntt_fail(NTT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                              \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+extern "C" const char *ntt_status_str(ntt_status s)
+{
+    switch (s) {
+    case NTT_OK: return "NTT_OK";
+    case NTT_ERR_LENGTH: return "NTT_ERR_LENGTH";
+    case NTT_ERR_MODULUS: return "NTT_ERR_MODULUS";
+    case NTT_ERR_WORD: return "NTT_ERR_WORD";
+    case NTT_ERR_RANGE: return "NTT_ERR_RANGE";
+    case NTT_ERR_OOM: return "NTT_ERR_OOM";
+    case NTT_ERR_CUDA: return "NTT_ERR_CUDA";
+    case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT";
+    case NTT_ERR_ARG: return "NTT_ERR_ARG";
+    case NTT_ERR_ADMISSION: return "NTT_ERR_ADMISSION";
+    }
+    return "NTT_ERR_UNKNOWN";
+}
+
+extern "C" const char *ntt_last_error(void) { return g_last_error; }
+
+// ------------------------------------------------------------------- plans
+
+struct ntt_plan_s {
+    uint64_t m = 0;
+    uint32_t N = 0;
+    int L = 0;
+    int word = 32;
+    uint64_t n_max = 0, omega = 0, n_inv = 0;
+    void *tw = nullptr;               // (z_i, z'_i) pairs, i < max(1, N/2)
+    ModC<uint32_t> c32{};
+    ModC<uint64_t> c64{};
+    bool split = false;
+    int LR = 0;
+    uint32_t wave = 0;                 // pairs per scratch wave (split path)
+    void *scratch = nullptr;           // 2 * wave * N words
+    int nsm = 1;
+    int device = 0;
+    unsigned long long *counter = nullptr;
+    // host-buffer path
+    void *stage = nullptr;
+    size_t stage_pairs = 0;
+    cudaStream_t hstream[2] = {nullptr, nullptr};
+    cudaEvent_t hevent[2] = {nullptr, nullptr};
+};
+
+template <typename W>
+static void fill_modc(ModC<W> &c, uint64_t m, uint64_t ninv)
+{
+    const int B = (int)sizeof(W) * 8;
+    c.m = (W)m;
+    c.m2 = (W)(2 * m);
+    c.mneg = (W)(0 - nt::inv_pow2(m, B));
+    const uint64_t cN = nt::shl_mod(ninv, B, m);
+    c.cN = (W)cN;
+    c.cNp = (W)nt::shoup_quot(cN, m, B);
+    c.onep = (W)nt::shoup_quot(1, m, B);
+    c.ninv = (W)ninv;
+    c.ninvp = (W)nt::shoup_quot(ninv, m, B);
+}
+
+static int num_sms()
+{
+    int dev = 0, n = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+extern "C" void ntt_plan_destroy(ntt_plan_t p)
+{
+    if (!p) return;
+    cudaFree(p->tw);
+    cudaFree(p->scratch);
+    cudaFree(p->counter);
+    cudaFree(p->stage);
+    for (int i = 0; i < 2; ++i) {
+        if (p->hstream[i]) cudaStreamDestroy(p->hstream[i]);
+        if (p->hevent[i]) cudaEventDestroy(p->hevent[i]);
+    }
+    delete p;
+}
+
+extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
+{
+    if (!out) return ntt_fail(NTT_ERR_ARG, "ntt_plan: out is NULL");
+    *out = nullptr;
+    if (m < 3 || !nt::is_prime(m)) return ntt_fail(NTT_ERR_MODULUS, "ntt_plan: m=%llu is not an odd prime", (unsigned long long)m);
+    if (m >= (1ull << 57)) return ntt_fail(NTT_ERR_WORD, "ntt_plan: m=%llu needs more than 57 bits", (unsigned long long)m);
+    const uint64_t nmax = nt::order_of_two_pow2(m);
+    if (nmax == 0) return ntt_fail(NTT_ERR_MODULUS, "ntt_plan: ord_m(2) is not a power of two for m=%llu", (unsigned long long)m);
+    if (N == 0 || (N & (N - 1)) != 0) return ntt_fail(NTT_ERR_LENGTH, "ntt_plan: N=%u is not a power of two", N);
+    if (nmax % N != 0) return ntt_fail(NTT_ERR_LENGTH, "ntt_plan: N=%u does not divide ord_m(2)=%llu", N, (unsigned long long)nmax);
+    const int word = m < (1ull << 25) ? 32 : 64;
+    const int L = __builtin_ctz(N);
+    const int lmax = word == 32 ? Launch<uint32_t>::LMAX : Launch<uint64_t>::LMAX;
+    if (L > lmax) return ntt_fail(NTT_ERR_LENGTH, "ntt_plan: N=2^%d above the supported 2^%d for %d-bit words", L, lmax, word);
+
+    auto p = std::unique_ptr<ntt_plan_s, void (*)(ntt_plan_t)>(new ntt_plan_s(), ntt_plan_destroy);
+    p->m = m; p->N = N; p->L = L; p->word = word; p->n_max = nmax;
+    p->omega = nt::pow_mod(2, nmax / N, m);
+    p->n_inv = nt::pow_mod(N % m, m - 2, m);            // Fermat: N^(m-2) = N^-1 for prime m
+    cudaGetDevice(&p->device);
+    p->nsm = num_sms();
+    const int lrmax = word == 32 ? Launch<uint32_t>::LRMAX : Launch<uint64_t>::LRMAX;
+    p->split = L > lrmax;
+    p->LR = p->split ? lrmax : L;
+
+    // Twiddles z_i = w^{brv_{L-1}(i)}, i < N/2, with w^e = 2^{e N_Max / N}
+    // generated by doubling modulo m (shift and conditional subtraction).
+    const size_t half = N > 1 ? N / 2 : 1;
+    std::vector<uint64_t> pw2 = nt::powers_of_two_by_doubling(N > 1 ? (nmax / N) * half : 1, m);
+    const int B = word;
+    const size_t elt = word / 8;
+    std::vector<unsigned char> host(2 * half * elt);
+    for (size_t i = 0; i < half; ++i) {
+        uint64_t z = 1;
+        if (N > 1) {
+            const uint64_t e = nt::bit_reverse(i, L - 1);
+            z = pw2[e * (nmax / N)];
+        }
+        const uint64_t zp = nt::shoup_quot(z, m, B);
+        if (word == 32) {
+            uint32_t a[2] = {(uint32_t)z, (uint32_t)zp};
+            memcpy(&host[2 * i * elt], a, sizeof a);
+        } else {
+            uint64_t a[2] = {z, zp};
+            memcpy(&host[2 * i * elt], a, sizeof a);
+        }
+    }
+    if (cudaMalloc(&p->tw, host.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twiddle table");
+    CUDA_TRY(cudaMemcpy(p->tw, host.data(), host.size(), cudaMemcpyHostToDevice), "ntt_plan: upload twiddles");
+    if (cudaMalloc(&p->counter, sizeof(unsigned long long)) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: counter");
+    if (word == 32) fill_modc(p->c32, m, p->n_inv);
+    else fill_modc(p->c64, m, p->n_inv);
+
+    if (p->split) {
+        // Enough pairs per wave to fill every SM with rows several times over,
+        // while the scratch (2 N words per pair) stays a few tens of MB.
+        const uint64_t rows_per_pair = 1ull << (L - p->LR);
+        uint64_t wave = (uint64_t)p->nsm * 4 / rows_per_pair;
+        if (wave < 1) wave = 1;
+        p->wave = (uint32_t)wave;
+        if (cudaMalloc(&p->scratch, 2 * wave * N * elt) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: scratch");
+    }
+    *out = p.release();
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_plan_get_info(ntt_plan_t p, ntt_plan_info_t *info)
+{
+    if (!p || !info) return ntt_fail(NTT_ERR_ARG, "ntt_plan_get_info: NULL argument");
+    memset(info, 0, sizeof *info);
+    info->m = p->m; info->N = p->N; info->log2N = (uint32_t)p->L; info->n_max = p->n_max;
+    info->omega = p->omega; info->n_inv = p->n_inv; info->word_bits = (uint32_t)p->word;
+    info->four_step = p->split ? 1u : 0u; info->wave = p->wave;
+    return NTT_OK;
+}
+
+extern "C" int ntt_plan_word_bits(ntt_plan_t p) { return p ? p->word : 0; }
+
+// ------------------------------------------------------------- dispatch
+
+template <typename W> static const ModC<W> &modc(ntt_plan_t p);
+template <> const ModC<uint32_t> &modc<uint32_t>(ntt_plan_t p) { return p->c32; }
+template <> const ModC<uint64_t> &modc<uint64_t>(ntt_plan_t p) { return p->c64; }
+
+static int row_grid(int nsm, long long rows, int per_block)
+{
+    long long blocks = (rows + per_block - 1) / per_block;
+    if (blocks > nsm) blocks = nsm;
+    return (int)(blocks > 0 ? blocks : 1);
+}
+
+// Fused convolution of `batch` pairs; src/dst modes: 0 contiguous arrays,
+// 1 descriptor list (descs, pair0 offsets into it).
+template <typename W>
+static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, const DevDesc<W> *descs,
+                                 long long pair0, long long batch, W *scratch, uint32_t wave, cudaStream_t st)
+{
+    const ModC<W> &c = modc<W>(p);
+    const W *tw = (const W *)p->tw;
+    const int mode = descs ? 1 : 0;
+    if (!p->split) {
+        RowArgs<W> a{f, g, h, descs, batch, pair0, tw, c};
+        return Launch<W>::conv_full(p->L, mode, a, row_grid(p->nsm, batch, Launch<W>::rows_per_block(p->L)), st);
+    }
+    const long long N = p->N;
+    for (long long w0 = 0; w0 < batch; w0 += wave) {
+        const long long np = std::min<long long>(wave, batch - w0);
+        ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c};
+        cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, ca, st);
+        if (e != cudaSuccess) return e;
+        const long long rows = np << (p->L - p->LR);
+        RowArgs<W> ra{scratch, scratch + (size_t)wave * N, scratch, nullptr, rows, 0, tw, c};
+        e = Launch<W>::conv_rows_split(p->L, ra, row_grid(p->nsm, rows, Launch<W>::rows_per_block(p->LR)), st);
+        if (e != cudaSuccess) return e;
+        e = Launch<W>::cols_inv(p->L, mode, ca, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename W>
+static cudaError_t ntt_dispatch(ntt_plan_t p, const W *x, W *y, long long batch, bool inv, cudaStream_t st)
+{
+    const ModC<W> &c = modc<W>(p);
+    const W *tw = (const W *)p->tw;
+    if (!p->split) {
+        NttArgs<W> a{x, y, batch, tw, c};
+        return Launch<W>::ntt_full(p->L, inv, a, row_grid(p->nsm, batch, Launch<W>::rows_per_block(p->L)), st);
+    }
+    const long long N = p->N;
+    W *scratch = (W *)p->scratch;
+    const long long wave = (long long)p->wave * 2;     // one sequence per pair: twice the pairs fit
+    for (long long w0 = 0; w0 < batch; w0 += wave) {
+        const long long np = std::min<long long>(wave, batch - w0);
+        ColArgs<W> ca{x, nullptr, nullptr, scratch, nullptr, nullptr, np, w0, tw, c};
+        cudaError_t e = Launch<W>::cols_fwd(p->L, 1, 0, ca, st);
+        if (e != cudaSuccess) return e;
+        const long long rows = np << (p->L - p->LR);
+        RowArgs<W> ra{scratch, nullptr, nullptr, nullptr, rows, 0, tw, c};
+        e = Launch<W>::rows_fwd(p->L, ra, row_grid(p->nsm, rows, Launch<W>::rows_per_block(p->LR)), st);
+        if (e != cudaSuccess) return e;
+        e = Launch<W>::bitrev_out(p->L, inv, scratch, y + (size_t)w0 * N, np, c, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+extern "C" ntt_status ntt_forward(ntt_plan_t p, const void *x, void *X, size_t batch, ntt_stream_t stream)
+{
+    if (!p || !x || !X || batch == 0) return ntt_fail(NTT_ERR_ARG, "ntt_forward: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = p->word == 32 ? ntt_dispatch<uint32_t>(p, (const uint32_t *)x, (uint32_t *)X, (long long)batch, false, st)
+                                  : ntt_dispatch<uint64_t>(p, (const uint64_t *)x, (uint64_t *)X, (long long)batch, false, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "ntt_forward");
+}
+
+extern "C" ntt_status ntt_inverse(ntt_plan_t p, const void *X, void *x, size_t batch, ntt_stream_t stream)
+{
+    if (!p || !x || !X || batch == 0) return ntt_fail(NTT_ERR_ARG, "ntt_inverse: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = p->word == 32 ? ntt_dispatch<uint32_t>(p, (const uint32_t *)X, (uint32_t *)x, (long long)batch, true, st)
+                                  : ntt_dispatch<uint64_t>(p, (const uint64_t *)X, (uint64_t *)x, (long long)batch, true, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "ntt_inverse");
+}
+
+extern "C" ntt_status conv_circular(ntt_plan_t p, const void *f, const void *g, void *h, size_t batch,
+                                    ntt_stream_t stream)
+{
+    if (!p || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = p->word == 32
+        ? conv_dispatch<uint32_t>(p, (const uint32_t *)f, (const uint32_t *)g, (uint32_t *)h, nullptr, 0,
+                                  (long long)batch, (uint32_t *)p->scratch, p->wave, st)
+        : conv_dispatch<uint64_t>(p, (const uint64_t *)f, (const uint64_t *)g, (uint64_t *)h, nullptr, 0,
+                                  (long long)batch, (uint64_t *)p->scratch, p->wave, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv_circular");
+}
+
+extern "C" ntt_status conv_circular_plain(ntt_plan_t p, const void *f, const void *g, void *h, size_t batch,
+                                          void *work, ntt_stream_t stream)
+{
+    if (!p || !f || !g || !h || !work || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular_plain: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = p->nsm * 8;
+    cudaError_t e = p->word == 32
+        ? Launch<uint32_t>::plain(p->L, (const uint32_t *)f, (const uint32_t *)g, (uint32_t *)h, (uint32_t *)work,
+                                  (long long)batch, (const uint32_t *)p->tw, p->c32, grid, st)
+        : Launch<uint64_t>::plain(p->L, (const uint64_t *)f, (const uint64_t *)g, (uint64_t *)h, (uint64_t *)work,
+                                  (long long)batch, (const uint64_t *)p->tw, p->c64, grid, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv_circular_plain");
+}
+
+extern "C" ntt_status ntt_check_range(ntt_plan_t p, const void *data, size_t count, uint64_t *bad,
+                                      ntt_stream_t stream)
+{
+    if (!p || !data) return ntt_fail(NTT_ERR_ARG, "ntt_check_range: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(p->counter, 0, sizeof(unsigned long long), st), "ntt_check_range: memset");
+    cudaError_t e = p->word == 32
+        ? Launch<uint32_t>::check_range((const uint32_t *)data, (long long)count, (uint32_t)p->m, p->counter, p->nsm * 4, st)
+        : Launch<uint64_t>::check_range((const uint64_t *)data, (long long)count, p->m, p->counter, p->nsm * 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ntt_check_range");
+    unsigned long long h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, p->counter, sizeof h, cudaMemcpyDeviceToHost, st), "ntt_check_range: copy");
+    CUDA_TRY(cudaStreamSynchronize(st), "ntt_check_range: sync");
+    if (bad) *bad = h;
+    return h ? ntt_fail(NTT_ERR_RANGE, "ntt_check_range: %llu words >= m", h) : NTT_OK;
+}
+
+// ------------------------------------------------------- host-buffer path
+
+extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void *g, void *h, size_t batch,
+                                         ntt_stream_t stream)
+{
+    if (!p || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular_host: invalid argument");
+    const size_t elt = p->word / 8;
+    const size_t seq = (size_t)p->N * elt;
+    // chunk of ~32 MB of input per pipeline slot, at least one pair
+    size_t chunk = std::max<size_t>(1, (size_t)(32u << 20) / (2 * seq));
+    chunk = std::min(chunk, batch);
+    if (!p->stage || p->stage_pairs < chunk) {
+        cudaFree(p->stage);
+        p->stage = nullptr;
+        if (cudaMalloc(&p->stage, 2 * 3 * chunk * seq) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "conv_circular_host: staging");
+        p->stage_pairs = chunk;
+        for (int i = 0; i < 2; ++i) {
+            if (!p->hstream[i]) CUDA_TRY(cudaStreamCreateWithFlags(&p->hstream[i], cudaStreamNonBlocking), "stream");
+            if (!p->hevent[i]) CUDA_TRY(cudaEventCreateWithFlags(&p->hevent[i], cudaEventDisableTiming), "event");
+        }
+    }
+    chunk = p->stage_pairs < chunk ? p->stage_pairs : chunk;
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaEvent_t start;
+    CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaEventRecord(start, user), "record");
+    for (int i = 0; i < 2; ++i) CUDA_TRY(cudaStreamWaitEvent(p->hstream[i], start, 0), "wait");
+    cudaEventDestroy(start);
+    const unsigned char *fb = (const unsigned char *)f, *gb = (const unsigned char *)g;
+    unsigned char *hb = (unsigned char *)h;
+    size_t slot = 0;
+    for (size_t b0 = 0; b0 < batch; b0 += chunk, slot ^= 1) {
+        const size_t nb = std::min(chunk, batch - b0);
+        cudaStream_t st = p->split ? p->hstream[0] : p->hstream[slot];   // split path shares scratch
+        unsigned char *base = (unsigned char *)p->stage + slot * 3 * chunk * seq;
+        void *df = base, *dg = base + chunk * seq, *dh = base + 2 * chunk * seq;
+        CUDA_TRY(cudaMemcpyAsync(df, fb + b0 * seq, nb * seq, cudaMemcpyHostToDevice, st), "H2D f");
+        CUDA_TRY(cudaMemcpyAsync(dg, gb + b0 * seq, nb * seq, cudaMemcpyHostToDevice, st), "H2D g");
+        ntt_status s = conv_circular(p, df, dg, dh, nb, (ntt_stream_t)st);
+        if (s != NTT_OK) return s;
+        CUDA_TRY(cudaMemcpyAsync(hb + b0 * seq, dh, nb * seq, cudaMemcpyDeviceToHost, st), "D2H h");
+    }
+    for (int i = 0; i < 2; ++i) {
+        CUDA_TRY(cudaEventRecord(p->hevent[i], p->hstream[i]), "record");
+        CUDA_TRY(cudaStreamWaitEvent(user, p->hevent[i], 0), "wait");
+    }
+    CUDA_TRY(cudaStreamSynchronize(user), "conv_circular_host: sync");
+    return NTT_OK;
+}
+
+int ntt_plan_log2(ntt_plan_t p) { return p ? p->L : -1; }
+
+ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs, long long count, void *scratch, uint32_t wave,
+                          cudaStream_t st)
+{
+    if (!p || !descs || count <= 0) return ntt_fail(NTT_ERR_ARG, "conv (descriptors): invalid argument");
+    if (p->split && (!scratch || wave == 0)) return ntt_fail(NTT_ERR_ARG, "conv (descriptors): split path needs scratch");
+    cudaError_t e = p->word == 32
+        ? conv_dispatch<uint32_t>(p, nullptr, nullptr, nullptr, (const DevDesc<uint32_t> *)descs, 0, count,
+                                  (uint32_t *)scratch, wave, st)
+        : conv_dispatch<uint64_t>(p, nullptr, nullptr, nullptr, (const DevDesc<uint64_t> *)descs, 0, count,
+                                  (uint64_t *)scratch, wave, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (descriptors)");
+}

@@ -1,0 +1,16 @@
+// ntt_internal.h -- functions shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "../../include/ntt_gb300.h"
+
+// Record a message for ntt_last_error() and return s.
+ntt_status ntt_fail(ntt_status s, const char *fmt, ...);
+// log2 N of a plan.
+int ntt_plan_log2(ntt_plan_t p);
+// Library-owned plan for (m, N), created on first use.
+ntt_status ntt_cached_plan(uint64_t m, uint32_t N, ntt_plan_t *out);
+// Fused convolution of `count` pairs given by a device descriptor list
+// {f, g, h} (three device pointers each); scratch/wave serve the split path.
+ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs_dev, long long count, void *scratch, uint32_t wave,
+                          cudaStream_t st);

@@ -1,0 +1,33 @@
+// ntt_launch.h -- host-side launchers of the kernels, one instantiation per
+// word type (launch_u32.cu / launch_u64.cu).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "ntt_kernels.cuh"
+
+namespace ntt {
+
+template <typename W> struct Launch {
+    static constexpr int LRMAX = LRMax<W>::v;
+    static constexpr int LMAX = LRMAX + 5;     // split path: up to 5 column bits
+    // rows transformed concurrently by one block of the row kernels
+    static int rows_per_block(int LR);
+    // whole-sequence fused convolution (L <= LRMAX); src 0 = contiguous, 1 = descriptors
+    static cudaError_t conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st);
+    // split path pieces (LRMAX < L <= LMAX)
+    static cudaError_t conv_rows_split(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
+    static cudaError_t cols_fwd(int L, int ns, int src, const ColArgs<W> &a, cudaStream_t st);
+    static cudaError_t cols_inv(int L, int dst, const ColArgs<W> &a, cudaStream_t st);
+    static cudaError_t rows_fwd(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
+    static cudaError_t bitrev_out(int L, bool inv, const W *src, W *dst, long long batch, const ModC<W> &c,
+                                  cudaStream_t st);
+    // natural-order transform of whole sequences (L <= LRMAX)
+    static cudaError_t ntt_full(int L, bool inv, const NttArgs<W> &a, int grid, cudaStream_t st);
+    // plain per-stage form
+    static cudaError_t plain(int L, const W *f, const W *g, W *h, W *work, long long batch, const W *tw,
+                             const ModC<W> &c, int grid, cudaStream_t st);
+    static cudaError_t check_range(const W *data, long long n, W m, unsigned long long *bad, int grid,
+                                   cudaStream_t st);
+};
+
+}  // namespace ntt

@@ -1,0 +1,256 @@
+"""Thin Python binding of the C ABI in ``include/ntt_gb300.h``.
+
+Argument marshalling only: every transform and convolution runs in the CUDA
+library ``libntt_gb300.so``.  Torch tensors serve as device buffers (their
+``data_ptr()``) and the current torch stream as the CUDA stream.  32-bit word
+plans take ``torch.int32`` / ``torch.uint32`` tensors, 64-bit word plans
+``torch.int64`` / ``torch.uint64``; values are residues in [0, m).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libntt_gb300.so")
+_lib = None
+
+NTT_OK = 0
+STATUS = {0: "NTT_OK", 1: "NTT_ERR_LENGTH", 2: "NTT_ERR_MODULUS", 3: "NTT_ERR_WORD", 4: "NTT_ERR_RANGE",
+          5: "NTT_ERR_OOM", 6: "NTT_ERR_CUDA", 7: "NTT_ERR_TIMEOUT", 8: "NTT_ERR_ARG", 9: "NTT_ERR_ADMISSION"}
+
+# Every function the header declares, with its ctypes signature.
+_VP, _U64, _U32, _SZ, _INT = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
+SIGNATURES = {
+    "ntt_status_str": (ctypes.c_char_p, [_INT]),
+    "ntt_last_error": (ctypes.c_char_p, []),
+    "ntt_plan": (_INT, [_U64, _U32, ctypes.POINTER(_VP)]),
+    "ntt_plan_destroy": (None, [_VP]),
+    "ntt_plan_get_info": (_INT, [_VP, _VP]),
+    "ntt_plan_word_bits": (_INT, [_VP]),
+    "ntt_forward": (_INT, [_VP, _VP, _VP, _SZ, _VP]),
+    "ntt_inverse": (_INT, [_VP, _VP, _VP, _SZ, _VP]),
+    "conv_circular": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
+    "conv_circular_plain": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "conv_circular_host": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
+    "conv_batched": (_INT, [_U64, _VP, _SZ, _VP]),
+    "ntt_batch_plan": (_INT, [_U64, _VP, _SZ, ctypes.POINTER(_VP)]),
+    "ntt_batch_exec": (_INT, [_VP, _VP]),
+    "ntt_batch_exec_graph": (_INT, [_VP, _VP]),
+    "ntt_batch_destroy": (None, [_VP]),
+    "ntt_check_range": (_INT, [_VP, _VP, _SZ, ctypes.POINTER(_U64), _VP]),
+}
+
+
+class NttError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}{': ' + detail if detail else ''}")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint64), ("N", ctypes.c_uint32), ("log2N", ctypes.c_uint32),
+                ("n_max", ctypes.c_uint64), ("omega", ctypes.c_uint64), ("n_inv", ctypes.c_uint64),
+                ("word_bits", ctypes.c_uint32), ("four_step", ctypes.c_uint32), ("wave", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class ConvDesc(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("g", ctypes.c_void_p), ("h", ctypes.c_void_p),
+                ("N", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+def lib():
+    """The loaded CUDA library.  Fails loudly when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1005_1497_gb300.build` "
+                               "(or __graft_entry__.build()); there is no fallback implementation")
+        so = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(so, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = so
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != NTT_OK:
+        raise NttError(status, where, lib().ntt_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+_DT = {32: (torch.int32, torch.uint32), 64: (torch.int64, torch.uint64)}
+
+
+class Plan:
+    """``ntt_plan(m, N)``: validated parameters and resident twiddle table."""
+
+    def __init__(self, m: int, N: int):
+        h = ctypes.c_void_p()
+        _check(lib().ntt_plan(m, N, ctypes.byref(h)), f"ntt_plan(m={m}, N={N})")
+        self.handle = h
+        info = PlanInfo()
+        _check(lib().ntt_plan_get_info(h, ctypes.byref(info)), "ntt_plan_get_info")
+        self.m, self.N, self.log2N = int(info.m), int(info.N), int(info.log2N)
+        self.n_max, self.omega, self.n_inv = int(info.n_max), int(info.omega), int(info.n_inv)
+        self.word_bits, self.four_step, self.wave = int(info.word_bits), bool(info.four_step), int(info.wave)
+        self.dtype = _DT[self.word_bits][0]
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().ntt_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, t: torch.Tensor, name: str) -> int:
+        """Validate a buffer of whole sequences; return its batch size."""
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype not in _DT[self.word_bits]:
+            raise TypeError(f"{name}: dtype {t.dtype} does not match {self.word_bits}-bit words")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() == 0 or t.numel() % self.N:
+            raise ValueError(f"{name}: {t.numel()} words is not a whole number of length-{self.N} sequences")
+        return t.numel() // self.N
+
+    def empty(self, batch: int, device="cuda") -> torch.Tensor:
+        return torch.empty((batch, self.N), dtype=self.dtype, device=device)
+
+
+def ntt_plan(m: int, N: int) -> Plan:
+    return Plan(m, N)
+
+
+def ntt_forward(plan: Plan, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    b = plan.check(x, "x")
+    out = torch.empty_like(x) if out is None else out
+    plan.check(out, "out")
+    _check(lib().ntt_forward(plan.handle, x.data_ptr(), out.data_ptr(), b, _stream(stream)), "ntt_forward")
+    return out
+
+
+def ntt_inverse(plan: Plan, X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    b = plan.check(X, "X")
+    out = torch.empty_like(X) if out is None else out
+    plan.check(out, "out")
+    _check(lib().ntt_inverse(plan.handle, X.data_ptr(), out.data_ptr(), b, _stream(stream)), "ntt_inverse")
+    return out
+
+
+def conv_circular(plan: Plan, f: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    b = plan.check(f, "f")
+    if plan.check(g, "g") != b:
+        raise ValueError("f and g hold different numbers of sequences")
+    out = torch.empty_like(f) if out is None else out
+    plan.check(out, "out")
+    _check(lib().conv_circular(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, _stream(stream)),
+           "conv_circular")
+    return out
+
+
+def conv_circular_plain(plan: Plan, f: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+                        work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    b = plan.check(f, "f")
+    if plan.check(g, "g") != b:
+        raise ValueError("f and g hold different numbers of sequences")
+    out = torch.empty_like(f) if out is None else out
+    work = torch.empty((2 * b, plan.N), dtype=f.dtype, device=f.device) if work is None else work
+    if work.numel() < 2 * b * plan.N:
+        raise ValueError("work must hold 2 * batch * N words")
+    _check(lib().conv_circular_plain(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, work.data_ptr(),
+                                     _stream(stream)), "conv_circular_plain")
+    return out
+
+
+def conv_circular_host(plan: Plan, f: torch.Tensor, g: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Host (ideally pinned) CPU tensors in and out; synchronous."""
+    for name, t in (("f", f), ("g", g), ("out", out)):
+        if t.is_cuda or not t.is_contiguous() or t.dtype not in _DT[plan.word_bits]:
+            raise ValueError(f"{name} must be a contiguous CPU tensor of {plan.word_bits}-bit words")
+    b = f.numel() // plan.N
+    if f.numel() != b * plan.N or g.numel() != f.numel() or out.numel() != f.numel():
+        raise ValueError("f, g, out must hold the same whole number of sequences")
+    _check(lib().conv_circular_host(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, _stream(stream)),
+           "conv_circular_host")
+    return out
+
+
+def _descs(triples):
+    arr = (ConvDesc * len(triples))()
+    keep = []
+    for i, (f, g, h) in enumerate(triples):
+        if not (f.is_cuda and g.is_cuda and h.is_cuda):
+            raise ValueError("conv_batched operands must be CUDA tensors")
+        if not (f.is_contiguous() and g.is_contiguous() and h.is_contiguous()):
+            raise ValueError("conv_batched operands must be contiguous")
+        if f.numel() != g.numel() or f.numel() != h.numel():
+            raise ValueError("f, g, h of one convolution must have the same length")
+        arr[i] = ConvDesc(f.data_ptr(), g.data_ptr(), h.data_ptr(), f.numel(), 0)
+        keep.append((f, g, h))
+    return arr, keep
+
+
+class BatchPlan:
+    """``ntt_batch_plan``: an uneven batch of convolutions modulo m."""
+
+    def __init__(self, m: int, triples):
+        self.descs, self._keep = _descs(triples)
+        h = ctypes.c_void_p()
+        _check(lib().ntt_batch_plan(m, ctypes.cast(self.descs, ctypes.c_void_p), len(triples), ctypes.byref(h)),
+               "ntt_batch_plan")
+        self.handle = h
+
+    def exec(self, stream=None):
+        _check(lib().ntt_batch_exec(self.handle, _stream(stream)), "ntt_batch_exec")
+
+    def exec_graph(self, stream=None):
+        _check(lib().ntt_batch_exec_graph(self.handle, _stream(stream)), "ntt_batch_exec_graph")
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().ntt_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ntt_batch_plan(m: int, triples) -> BatchPlan:
+    return BatchPlan(m, triples)
+
+
+def conv_batched(m: int, triples, stream=None):
+    """Convolve a list of (f, g, h) CUDA tensors of power-of-two lengths mod m."""
+    arr, _keep = _descs(triples)
+    _check(lib().conv_batched(m, ctypes.cast(arr, ctypes.c_void_p), len(triples), _stream(stream)), "conv_batched")
+
+
+def ntt_check_range(plan: Plan, x: torch.Tensor, stream=None) -> int:
+    """Number of words of x that are >= m (synchronous)."""
+    bad = ctypes.c_uint64(0)
+    st = lib().ntt_check_range(plan.handle, x.data_ptr(), x.numel(), ctypes.byref(bad), _stream(stream))
+    if st not in (NTT_OK, 4):
+        _check(st, "ntt_check_range")
+    return int(bad.value)

@@ -1,0 +1,69 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function the
+header declares, and the host-side plan validation rejects bad parameters
+before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "ntt_gb300.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_0-9]+)\s*\([^;{]*\)\s*;", src)) - {"sizeof"})
+
+
+@pytest.fixture(scope="module")
+def ntt():
+    from paper_1005_1497_gb300 import build, ntt as mod
+    build.build()
+    return mod
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ntt_plan", "ntt_forward", "ntt_inverse", "conv_circular", "conv_batched", "ntt_status_str"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(ntt):
+    so = ctypes.CDLL(ntt.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(so, n)]
+    assert missing == []
+    assert set(_declared()) == set(ntt.SIGNATURES)
+
+
+def test_status_strings(ntt):
+    lib = ntt.lib()
+    for code, name in ntt.STATUS.items():
+        assert lib.ntt_status_str(code).decode() == name
+
+
+@pytest.mark.parametrize("m,N,status", [
+    (341, 8, 2),            # Sec. II: 341 = 11 * 31 is composite
+    (13631487, 8, 2),       # composite neighbour
+    (7, 2, 2),              # ord_7(2) = 3 is not a power of two (Fig. 1 (c))
+    (13631489, 3, 1),       # not a power of two
+    (13631489, 1 << 20, 1), # does not divide ord = 2^19 (Sec. I)
+    (641, 128, 1),          # Table 1: 641 allows N <= 64
+    (2424833, 2048, 1),     # Table 1: N_Max = 1024
+    (13631489, 0, 1),
+])
+def test_plan_rejects(ntt, m, N, status):
+    h = ctypes.c_void_p()
+    assert ntt.lib().ntt_plan(m, N, ctypes.byref(h)) == status
+    assert not h.value
+    assert ntt.lib().ntt_last_error().decode()
+
+
+def test_null_arguments(ntt):
+    lib = ntt.lib()
+    assert lib.ntt_plan(13631489, 8, None) == 8
+    assert lib.ntt_forward(None, None, None, 1, None) == 8
+    assert lib.conv_circular(None, None, None, None, 1, None) == 8
+    assert lib.conv_batched(13631489, None, 0, None) == 8

@@ -1,0 +1,207 @@
+"""Parity of the CUDA path with the CPU oracle: every result bit-exact.
+
+Sizes span several thread-block tiles and ragged batch tails; lengths above
+one block exercise the split (column + row) path.  The oracle is the direct
+definition (Eq. 1-3) up to N = 2^12 and the textbook radix-2 algorithm above,
+which the oracle pins tie to the definition; at the full benchmark sizes a
+sample of outputs is recomputed one by one from Eq. 1."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import M, M64, TABLE1, dev, host, need_gpu, pairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ntt():
+    need_gpu()
+    from paper_1005_1497_gb300 import ntt as mod
+    mod.lib()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.Oracle()
+
+
+def ref_conv(orc, f, g, m, w):
+    N = f.shape[-1]
+    fn = (lambda a, b: orc.conv(a, b, m)) if N <= 4096 else (lambda a, b: orc.fast_conv(a, b, m, w))
+    return oracle.batched(fn, f, g)
+
+
+def ref_ntt(orc, x, m, w, inverse=False):
+    N = x.shape[-1]
+    if N <= 4096:
+        fn = (lambda a: orc.intt(a, m, w)) if inverse else (lambda a: orc.ntt(a, m, w))
+    else:
+        winv = orc.mod_inverse(w, m)
+        ninv = orc.mod_inverse(N % m, m)
+        if inverse:
+            fn = lambda a: np.array([orc.mod_mul(int(v), ninv, m) for v in orc.fast_ntt(a, m, winv)], dtype=np.uint64)
+        else:
+            fn = lambda a: orc.fast_ntt(a, m, w)
+    return oracle.batched(fn, x)
+
+
+CASES32 = [(m, L) for m, lmax in TABLE1 for L in sorted({0, 1, 2, 3, 5, 6, lmax} | set(range(7, min(lmax, 14) + 1)))
+           if L <= lmax]
+
+
+@pytest.mark.parametrize("m,L", CASES32)
+def test_conv_u32(ntt, orc, m, L):
+    N = 1 << L
+    batch = 3 if L >= 10 else 37            # ragged against rows per block
+    plan = ntt.Plan(m, N)
+    assert plan.word_bits == 32
+    f, g = pairs(m, batch, N, seed=100 + L)
+    h = host(ntt.conv_circular(plan, dev(f, 32), dev(g, 32)))
+    torch.cuda.synchronize()
+    assert np.array_equal(h, ref_conv(orc, f, g, m, plan.omega))
+
+
+@pytest.mark.parametrize("L", [15, 16, 17, 18, 19])
+def test_conv_u32_split(ntt, orc, L):
+    N = 1 << L
+    plan = ntt.Plan(M, N)
+    assert plan.four_step
+    batch = plan.wave + 1                   # two waves, the second ragged
+    f, g = pairs(M, batch, N, seed=200 + L)
+    h = host(ntt.conv_circular(plan, dev(f, 32), dev(g, 32)))
+    torch.cuda.synchronize()
+    want = ref_conv(orc, f[:2], g[:2], M, plan.omega)
+    assert np.array_equal(h[:2], want)
+    # the rest of the batch by sampled outputs (Eq. 1 one index at a time)
+    rng = np.random.default_rng(L)
+    for b in range(2, batch, max(1, batch // 6)):
+        idx = rng.integers(0, N, 48, dtype=np.uint64)
+        assert np.array_equal(h[b][idx.astype(np.int64)], orc.conv_sample(f[b], g[b], M, idx))
+
+
+@pytest.mark.parametrize("L", [0, 1, 3, 4, 5, 8, 12, 13, 14, 15, 16, 18])
+def test_conv_u64(ntt, orc, L):
+    N = 1 << L
+    plan = ntt.Plan(M64, N)
+    assert plan.word_bits == 64
+    batch = 2 if L >= 13 else 19
+    f, g = pairs(M64, batch, N, seed=300 + L)
+    h = host(ntt.conv_circular(plan, dev(f, 64), dev(g, 64)))
+    torch.cuda.synchronize()
+    assert np.array_equal(h, ref_conv(orc, f, g, M64, plan.omega))
+
+
+@pytest.mark.parametrize("m,L", [(641, 6), (2424833, 10), (M, 1), (M, 7), (M, 11), (M, 14), (M, 15), (M, 19),
+                                 (M64, 9), (M64, 14)])
+def test_ntt_forward_inverse(ntt, orc, m, L):
+    N = 1 << L
+    plan = ntt.Plan(m, N)
+    wb = plan.word_bits
+    batch = 3
+    x, _ = pairs(m, batch, N, seed=400 + L)
+    X = ntt.ntt_forward(plan, dev(x, wb))
+    Xh = host(X)
+    want = ref_ntt(orc, x, m, plan.omega)
+    assert np.array_equal(Xh, want)
+    back = host(ntt.ntt_inverse(plan, X))
+    assert np.array_equal(back, x)
+    # the inverse on its own input against Eq. 3
+    assert np.array_equal(host(ntt.ntt_inverse(plan, dev(x, wb))), ref_ntt(orc, x, m, plan.omega, inverse=True))
+
+
+@pytest.mark.parametrize("m,L", [(M, 0), (M, 1), (M, 5), (M, 10), (M, 14), (M, 16), (M64, 11), (641, 6)])
+def test_conv_plain_form(ntt, orc, m, L):
+    N = 1 << L
+    plan = ntt.Plan(m, N)
+    f, g = pairs(m, 5, N, seed=500 + L)
+    h = host(ntt.conv_circular_plain(plan, dev(f, plan.word_bits), dev(g, plan.word_bits)))
+    assert np.array_equal(h, ref_conv(orc, f, g, m, plan.omega))
+
+
+@pytest.mark.parametrize("m", [M, M64])
+@pytest.mark.parametrize("L", [1, 6, 10, 14, 17])
+def test_extreme_inputs(ntt, orc, m, L):
+    """All words m-1 (the lazy bounds' worst case): h(j) = N (m-1)^2 = N mod m."""
+    N = 1 << L
+    if m == M64 and L > 18:
+        pytest.skip()
+    plan = ntt.Plan(m, N)
+    wb = plan.word_bits
+    f = np.full((2, N), m - 1, dtype=np.uint64)
+    h = host(ntt.conv_circular(plan, dev(f, wb), dev(f, wb)))
+    assert np.all(h == N % m)
+    z = np.zeros((1, N), dtype=np.uint64)
+    assert not host(ntt.conv_circular(plan, dev(z, wb), dev(f[:1], wb))).any()
+    X = host(ntt.ntt_forward(plan, dev(f[:1], wb)))
+    assert X[0, 0] == (N * (m - 1)) % m and not X[0, 1:].any()
+
+
+def test_in_place_and_deterministic(ntt, orc):
+    for L in (9, 14, 16):
+        N = 1 << L
+        plan = ntt.Plan(M, N)
+        f, g = pairs(M, 4, N, seed=600 + L)
+        ft, gt = dev(f, 32), dev(g, 32)
+        h1 = host(ntt.conv_circular(plan, ft, gt))
+        h2 = host(ntt.conv_circular(plan, ft, gt))
+        assert np.array_equal(h1, h2)
+        ntt.conv_circular(plan, ft, gt, out=ft)          # h aliases f
+        assert np.array_equal(host(ft), h1)
+
+
+def test_conv_batched_uneven(ntt, orc):
+    from paper_1005_1497_gb300 import inputs
+    lens = inputs.log_uniform_lengths(60, 0, 19, seed=7)
+    triples, ref = [], []
+    for i, N in enumerate(lens):
+        N = int(N)
+        f, g = pairs(M, 1, N, seed=700 + i)
+        triples.append((dev(f[0], 32), dev(g[0], 32), torch.empty(N, dtype=torch.int32, device="cuda")))
+        ref.append((f[0], g[0], N))
+    ntt.conv_batched(M, triples)
+    torch.cuda.synchronize()
+    w_of = {}
+    for (f, g, N), (_, _, h) in zip(ref, triples):
+        hh = host(h)
+        if N <= 1024:
+            assert np.array_equal(hh, orc.conv(f, g, M))
+        else:
+            idx = np.random.default_rng(N).integers(0, N, 32, dtype=np.uint64)
+            assert np.array_equal(hh[idx.astype(np.int64)], orc.conv_sample(f, g, M, idx))
+    # graph replay gives the same results
+    bp = ntt.BatchPlan(M, triples)
+    outs = [host(h).copy() for _, _, h in triples]
+    for _, _, h in triples:
+        h.zero_()
+    bp.exec_graph()
+    bp.exec_graph()
+    torch.cuda.synchronize()
+    for o, (_, _, h) in zip(outs, triples):
+        assert np.array_equal(host(h), o)
+    bp.close()
+
+
+def test_check_range(ntt):
+    plan = ntt.Plan(M, 1 << 10)
+    x = torch.zeros(5000, dtype=torch.int32, device="cuda")
+    assert ntt.ntt_check_range(plan, x) == 0
+    x[17] = M
+    x[4000] = M + 5
+    assert ntt.ntt_check_range(plan, x) == 2
+
+
+def test_host_buffers(ntt, orc):
+    for L in (10, 16):
+        N = 1 << L
+        plan = ntt.Plan(M, N)
+        f, g = pairs(M, 9, N, seed=800 + L)
+        ft = torch.from_numpy(f.astype(np.int32)).pin_memory()
+        gt = torch.from_numpy(g.astype(np.int32)).pin_memory()
+        ht = torch.empty_like(ft).pin_memory()
+        ntt.conv_circular_host(plan, ft, gt, ht)
+        want = host(ntt.conv_circular(plan, ft.cuda(), gt.cuda()))
+        assert np.array_equal(ht.numpy().astype(np.uint64), want)
+        assert np.array_equal(want[:1], ref_conv(orc, f[:1], g[:1], M, plan.omega))
