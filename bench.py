@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact digital circular convolution on GB300.
+
+One step = one fused batched convolution (forward transforms of f and g,
+pointwise product with N^-1, inverse transform) over the whole workload,
+inputs resident in HBM.  Default workload: 4096 pairs, N = 2^14,
+m = 13631489, 32-bit words (the uniform-batch configuration).  Prints ONE
+JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload conv2|conv1|conv3|conv4] [--quick]
+
+Multi-GPU (torchrun): every rank convolves its own batch (independent pairs,
+no collective on the data path); the timing is the max over ranks and the
+value counts the pairs of all ranks (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = 13631489
+METRIC = "circular convolutions/sec and NTT GB/s vs HBM peak, batched vs plain form, bit-exact"
+WORKLOADS = {
+    # name: (batch, log2N, description)
+    "conv2": (4096, 14, "uniform batch: 4096 pairs x N=2^14, m=13631489, uint32"),
+    "conv1": (1, 10, "single convolution: 1 pair x N=2^10, m=13631489, uint32"),
+    "conv3": (64, 19, "large transforms: 64 pairs x N=2^19, m=13631489, uint32, split column/row path"),
+}
+IMAD_PER_SM_CLK = 64          # 32-bit IMAD lanes per SM per clock (measured on GB300)
+SLOTS_PER_MODMUL = 4          # Shoup product: IMAD.HI (2 issue slots of the IMAD pipe) + 2 IMAD
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="conv2", choices=sorted(WORKLOADS))
+    ap.add_argument("--quick", action="store_true", help="fused timing only (no plain form, e2e, CPU baseline)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_from_profile(kernel_tag: str):
+    """DRAM bytes per launch recorded by an ncu capture summary in profiles/, if
+    it was taken on the current kernel sources (digest line matches)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    from paper_1005_1497_gb300 import build
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("sources_digest") != build.sources_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(f, g, m: int, budget_s: float, threads: int | None = None):
+    """Oracle (direct Eq. 1) throughput on the host cores, on a bounded sample
+    of the workload's pairs: consecutive blocks of output indices of
+    consecutive pairs, as many as fit the time budget.  Returns
+    (conv/s, threads, outputs computed, seconds)."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle()
+    threads = threads or os.cpu_count() or 1
+    N = f.shape[1]
+    block = max(1, min(N, 256))
+    stop = time.perf_counter() + budget_s
+    lock = threading.Lock()
+    state = {"next": 0, "done": 0}
+
+    def worker():
+        while time.perf_counter() < stop:
+            with lock:
+                k = state["next"]
+                state["next"] += 1
+            pair, off = divmod(k * block, N)
+            pair %= f.shape[0]
+            idx = np.arange(off, off + block, dtype=np.uint64)
+            o.conv_sample(f[pair], g[pair], m, idx)
+            with lock:
+                state["done"] += block
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    el = time.perf_counter() - t0
+    return state["done"] / N / el, threads, state["done"], el
+
+
+# ---------------------------------------------------------------- our path
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1005_1497_gb300 import inputs, ntt
+
+    world, rank, local = dist_setup()
+    batch, L, desc = WORKLOADS[args.workload]
+    N = 1 << L
+    plan = ntt.Plan(M, N)
+    # inputs generated on the host from the shared seeded generator, then resident in HBM
+    f_np, g_np = inputs.pairs(M, batch, N, seed=1000 + rank)
+    f = torch.from_numpy(f_np.view(np.int32)).cuda()
+    g = torch.from_numpy(g_np.view(np.int32)).cuda()
+    h = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+    launches_per_step = 1 if not plan.four_step else 3 * -(-batch // plan.wave)
+
+    def step():
+        ntt.conv_circular(plan, f, g, out=h, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(world, ms)
+    clocks = clk.summary()
+    pairs_total = batch * world
+    value = pairs_total * 1000.0 / ms
+
+    # roofline of the fused kernel (one launch per step when N fits one block)
+    hbm_peak, sm_max_mhz, peak_src = peaks()
+    alg_bytes = 12.0 * N * batch                                 # f, g in, h out (uint32)
+    modmul = batch * (3 * (N // 2) * L + N)                      # butterfly products + pointwise
+    launch_ms = ms / launches_per_step
+    alu_peak = torch.cuda.get_device_properties(local).multi_processor_count * IMAD_PER_SM_CLK \
+        * sm_max_mhz * 1e6 / SLOTS_PER_MODMUL / 1e9               # G modmul/s
+    alu_ach = modmul / (ms * 1e-3) / 1e9
+    hbm_ach = alg_bytes / (ms * 1e-3) / 1e9
+    kernel_tag = f"k_conv_rows_u32_L{L}_{batch}x{N}"
+    traffic = traffic_from_profile(kernel_tag) if not plan.four_step else None
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "conv/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded counter-based uniform residues in [0,m))",
+        "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "m": M, "form": "fused batched",
+                   "l2": "inputs larger than L2 (512 MiB f+g at conv2); no flush",
+                   "parallelism": f"replicas x{world} (independent pairs per GPU)"},
+        "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
+                     "frac": round(alu_ach / alu_peak, 4), "traffic": traffic,
+                     "peak_src": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x SMs x {sm_max_mhz:.0f} MHz / {SLOTS_PER_MODMUL} slots per Shoup product",
+                     "kernel": kernel_tag if not plan.four_step else "split path (3 kernels per wave)",
+                     "launch_ms": round(launch_ms, 4)},
+        "roofline_hbm": {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(hbm_ach / hbm_peak, 4), "peak_src": f"{peak_src} copy bandwidth",
+                         "algorithmic_bytes_per_step": alg_bytes},
+        "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+
+    if not args.quick:
+        # plain form: one launch per butterfly stage over the whole batch
+        work = torch.empty((2 * batch, N), dtype=torch.int32, device="cuda")
+        h2 = torch.empty_like(f)
+        for _ in range(max(args.warmup, 1)):
+            ntt.conv_circular_plain(plan, f, g, out=h2, work=work, stream=stream)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        psteps = max(1, min(args.steps // 2, 100))
+        p0.record(stream)
+        for _ in range(psteps):
+            ntt.conv_circular_plain(plan, f, g, out=h2, work=work, stream=stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(world, p0.elapsed_time(p1) / psteps)
+        same = bool(torch.equal(h, h2))
+        out["plain_form"] = {"value": round(pairs_total * 1000.0 / pms, 1), "unit": "conv/s",
+                             "ms_per_step": round(pms, 4), "launches_per_step": 2 * L + 2,
+                             "algorithmic_GBps": round(alg_bytes / (pms * 1e-3) / 1e9, 1),
+                             "fused_speedup": round(pms / ms, 2), "bit_identical_to_fused": same}
+        del work, h2
+
+        # end to end through the host-buffer entry point (pinned host memory)
+        fh = torch.from_numpy(f_np.view(np.int32)).pin_memory()
+        gh = torch.from_numpy(g_np.view(np.int32)).pin_memory()
+        hh = torch.empty_like(fh).pin_memory()
+        ntt.conv_circular_host(plan, fh, gh, hh, stream=stream)
+        esteps = max(1, min(args.steps, 20))
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            ntt.conv_circular_host(plan, fh, gh, hh, stream=stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(world, (time.perf_counter() - t0) * 1000.0 / esteps)
+        out["e2e"] = {"value": round(pairs_total * 1000.0 / ems, 1), "unit": "conv/s", "ms_per_step": round(ems, 3),
+                      "h2d_bytes_per_step": 2 * batch * N * 4, "d2h_bytes_per_step": batch * N * 4,
+                      "entry": "conv_circular_host (pinned host buffers, chunked copy/compute overlap)",
+                      "bit_identical_to_device_path": bool(torch.equal(hh, h.cpu()))}
+        if world == 1 and rank == 0:
+            rate, thr, done, el = cpu_oracle_rate(f_np, g_np, M, args.cpu_seconds)
+            out["cpu_baseline"] = {"value": round(rate, 4), "unit": "conv/s", "cores": thr, "kind": "oracle",
+                                   "sample": f"direct Eq. 1 (oracle or_conv_sample) on {done} output indices "
+                                             f"(= {done / N:.2f} of the {batch} length-{N} pairs) in {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle, as it stands, timed on the host cores on bounded samples of
+    the same workload (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1005_1497_gb300 import inputs
+    batch, L, desc = WORKLOADS[args.workload]
+    N = 1 << L
+    f, g = inputs.pairs(M, min(batch, 64), N, seed=1000)
+    per_step = max(1.0, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(f, g, M, per_step / 4)
+    rates, total_done, total_el, thr = [], 0, 0.0, 1
+    for _ in range(args.steps):
+        r, thr, done, el = cpu_oracle_rate(f, g, M, per_step)
+        rates.append(r)
+        total_done += done
+        total_el += el
+    value = total_done / N / total_el
+    sample = f"direct Eq. 1 on {total_done} output indices of the first {f.shape[0]} pairs, {per_step:.1f} s per step"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "conv/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / value * batch, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (oracle, __int128 products)",
+           "data": "synthetic (seeded counter-based uniform residues in [0,m))",
+           "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "m": M, "form": "CPU oracle"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "conv/s", "cores": thr, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "conv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

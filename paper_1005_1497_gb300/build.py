@@ -79,5 +79,16 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     return LIB
 
 
+
+def sources_digest() -> str:
+    """Digest of every CUDA source and header plus the flags: identifies the
+    kernels a profile summary was captured on."""
+    h = hashlib.sha256(_headers_digest().encode())
+    for src in _sources():
+        with open(os.path.join(CSRC, src), "rb") as fh:
+            h.update(src.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
