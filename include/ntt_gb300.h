@@ -186,6 +186,36 @@ ntt_status ntt_batch_exec_graph(ntt_batch_t batch, ntt_stream_t stream);
 
 void ntt_batch_destroy(ntt_batch_t batch);
 
+/* --------------------------------------------------- no-allocation variant */
+
+/* Size in bytes of the library's static split-path scratch (per GPU). */
+#define NTT_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* conv_circular for callers that cannot allocate device memory when they
+ * convolve: programs whose device memory belongs to another allocator (a
+ * framework pool that has reserved the GPU, a fixed memory map) and loops
+ * that cannot afford cudaMalloc/cudaFree, which may synchronise the device.
+ * The paper has no counterpart; this is an interface choice of the library.
+ *
+ * Same arguments, layout, ownership and result as conv_circular.  The call
+ * allocates nothing: lengths that fit one thread block need no scratch, and
+ * longer ones (the split path) use one static array of
+ * NTT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
+ * holds until the process exits.  The batch is processed in waves of
+ * floor(16 MiB / (2 N word_bytes)) pairs; a length whose single pair needs
+ * more than the array is rejected with NTT_ERR_ARG (no supported length
+ * does today).  The plan must be created beforehand (ntt_plan allocates).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one array
+ * and it keeps the last call's contents; nothing in it needs clearing, but
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it and must be serialised by the caller.
+ * Errors: NTT_ERR_ARG, NTT_ERR_CUDA. */
+ntt_status conv_circular_noalloc(ntt_plan_t plan, const void *f_dev, const void *g_dev, void *h_dev,
+                                 size_t batch, ntt_stream_t stream);
+
 /* ----------------------------------------------------------------- checks */
 
 /* Count the words of `count` words at data_dev (word size of the plan) that

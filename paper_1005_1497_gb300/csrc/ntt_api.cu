@@ -403,3 +403,16 @@ ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs, long long count, void
                                   (uint64_t *)scratch, wave, st);
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (descriptors)");
 }
+
+ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, void *h, long long batch,
+                                 void *scratch, uint32_t wave, cudaStream_t st)
+{
+    if (!p || !f || !g || !h || batch <= 0) return ntt_fail(NTT_ERR_ARG, "conv (scratch): invalid argument");
+    if (p->split && (!scratch || wave == 0)) return ntt_fail(NTT_ERR_ARG, "conv (scratch): split path needs scratch");
+    cudaError_t e = p->word == 32
+        ? conv_dispatch<uint32_t>(p, (const uint32_t *)f, (const uint32_t *)g, (uint32_t *)h, nullptr, 0, batch,
+                                  (uint32_t *)scratch, wave, st)
+        : conv_dispatch<uint64_t>(p, (const uint64_t *)f, (const uint64_t *)g, (uint64_t *)h, nullptr, 0, batch,
+                                  (uint64_t *)scratch, wave, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (scratch)");
+}

@@ -14,3 +14,7 @@ ntt_status ntt_cached_plan(uint64_t m, uint32_t N, ntt_plan_t *out);
 // {f, g, h} (three device pointers each); scratch/wave serve the split path.
 ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs_dev, long long count, void *scratch, uint32_t wave,
                           cudaStream_t st);
+// Fused convolution of contiguous [batch][N] arrays with caller-chosen
+// split-path scratch (wave pairs of 2 N words); scratch unused when N fits one block.
+ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, void *h, long long batch,
+                                 void *scratch, uint32_t wave, cudaStream_t st);

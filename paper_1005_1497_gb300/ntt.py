@@ -35,6 +35,7 @@ SIGNATURES = {
     "conv_circular": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
     "conv_circular_plain": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "conv_circular_host": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
+    "conv_circular_noalloc": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
     "conv_batched": (_INT, [_U64, _VP, _SZ, _VP]),
     "ntt_batch_plan": (_INT, [_U64, _VP, _SZ, ctypes.POINTER(_VP)]),
     "ntt_batch_exec": (_INT, [_VP, _VP]),
@@ -191,6 +192,18 @@ def conv_circular_host(plan: Plan, f: torch.Tensor, g: torch.Tensor, out: torch.
         raise ValueError("f, g, out must hold the same whole number of sequences")
     _check(lib().conv_circular_host(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, _stream(stream)),
            "conv_circular_host")
+    return out
+
+
+def conv_circular_noalloc(plan: Plan, f: torch.Tensor, g: torch.Tensor, out: torch.Tensor,
+                          stream=None) -> torch.Tensor:
+    """conv_circular that allocates nothing (``out`` must be given); uses the
+    library's static scratch, see the header for the sharing rules."""
+    b = plan.check(f, "f")
+    if plan.check(g, "g") != b or plan.check(out, "out") != b:
+        raise ValueError("f, g and out must hold the same number of sequences")
+    _check(lib().conv_circular_noalloc(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b,
+                                       _stream(stream)), "conv_circular_noalloc")
     return out
 
 
