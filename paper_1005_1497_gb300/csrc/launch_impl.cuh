@@ -21,18 +21,35 @@ int Launch<W>::rows_per_block(int LR)
     return BLOCK >> (LR - RL);
 }
 
+// Whole sequences: rows that fit one warp run the warp-level kernel; longer
+// ones (up to one block) the column/row kernel.
 template <typename W, int L, int SRC>
 static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t st)
 {
-    if constexpr (L <= LRMax<W>::v) {
-        constexpr size_t smem = RowShape<W, L, L>::smem(2);
-        static const cudaError_t init = ensure_smem(k_conv_rows<W, L, L, SRC>, smem);
+    constexpr int RW = Arith<W>::RB + 5;
+    if constexpr (L <= RW) {
+        constexpr size_t smem = TwBytes<W, L>::v + RowShape<W, L, L>::smem(2);
+        static const cudaError_t init = ensure_smem(k_conv_fused<W, L, SRC>, smem);
         if (init != cudaSuccess) return init;
-        k_conv_rows<W, L, L, SRC><<<grid, BLOCK, smem, st>>>(a);
+        k_conv_fused<W, L, SRC><<<grid, BLOCK, smem, st>>>(a);
+        return cudaGetLastError();
+    } else if constexpr (L <= LRMax<W>::v) {
+        constexpr size_t smem = CRShape<W, L>::smem;
+        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, SRC>, smem);
+        if (init != cudaSuccess) return init;
+        k_conv_cr<W, L, SRC><<<grid, BLOCK, smem, st>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
     }
+}
+
+template <typename W>
+int Launch<W>::pairs_per_block(int L)
+{
+    const int RW = Arith<W>::RB + 5;
+    if (L <= RW) return rows_per_block(L);
+    return BLOCK / (32 << (L - RW));
 }
 
 template <typename W, int L>
@@ -97,7 +114,7 @@ template <typename W, int L, bool INV>
 static cudaError_t launch_ntt_full(const NttArgs<W> &a, int grid, cudaStream_t st)
 {
     if constexpr (L <= LRMax<W>::v) {
-        constexpr size_t smem = RowShape<W, L, L>::smem(1);
+        constexpr size_t smem = TwBytes<W, L>::v + RowShape<W, L, L>::smem(1);
         static const cudaError_t init = ensure_smem(k_ntt_rows<W, L, INV>, smem);
         if (init != cudaSuccess) return init;
         k_ntt_rows<W, L, INV><<<grid, BLOCK, smem, st>>>(a);

@@ -2,5 +2,6 @@
 #include "launch_impl.cuh"
 namespace ntt {
 template int Launch<uint64_t>::rows_per_block(int);
+template int Launch<uint64_t>::pairs_per_block(int);
 template cudaError_t Launch<uint64_t>::conv_full(int, int, const RowArgs<uint64_t> &, int, cudaStream_t);
 }  // namespace ntt

@@ -232,7 +232,7 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     const int mode = descs ? 1 : 0;
     if (!p->split) {
         RowArgs<W> a{f, g, h, descs, batch, pair0, tw, c};
-        return Launch<W>::conv_full(p->L, mode, a, row_grid(p->nsm, batch, Launch<W>::rows_per_block(p->L)), st);
+        return Launch<W>::conv_full(p->L, mode, a, row_grid(p->nsm, batch, Launch<W>::pairs_per_block(p->L)), st);
     }
     const long long N = p->N;
     for (long long w0 = 0; w0 < batch; w0 += wave) {

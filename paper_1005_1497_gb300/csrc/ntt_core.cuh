@@ -183,31 +183,75 @@ __device__ __forceinline__ void group_sync(int gid)
     }
 }
 
-// Load the twiddle pairs z_i, z'_i for i = nb .. nb + CNT - 1 (nb aligned to CNT).
-template <typename W, int CNT>
-__device__ __forceinline__ void load_tw(const W *__restrict__ tw, uint32_t nb, W (&z)[CNT], W (&zp)[CNT])
+// Twiddle sources.  TW_GLOBAL: the plan's table in device memory, read
+// through the read-only cache.  TW_SMEM: a copy in shared memory laid out in
+// 16-byte chunks with an XOR swizzle: chunk c of 128-byte row r is stored at
+// position c ^ fold(r), fold(r) = XOR of the 3-bit groups of r.  Folding all
+// row bits (not just the low three) keeps every level's per-thread runs on
+// distinct banks, including the inverse's runs whose rows are bit-reversed
+// thread indices and so differ only in high bits.
+enum { TW_GLOBAL = 0, TW_SMEM = 1 };
+
+__host__ __device__ constexpr uint32_t tw_fold(uint32_t row)
 {
-    if constexpr (sizeof(W) == 4 && CNT >= 2) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(tw) + (nb >> 1);
-#pragma unroll
-        for (int t = 0; t < CNT / 2; ++t) {
-            uint4 q = __ldg(p + t);
-            z[2 * t] = (W)q.x; zp[2 * t] = (W)q.y; z[2 * t + 1] = (W)q.z; zp[2 * t + 1] = (W)q.w;
+    return (row ^ (row >> 3) ^ (row >> 6) ^ (row >> 9) ^ (row >> 12) ^ (row >> 15)) & 7u;
+}
+__host__ __device__ constexpr uint32_t tw_swz(uint32_t chunk) { return chunk ^ tw_fold(chunk >> 3); }
+
+// Pairs per 16-byte chunk of the table.
+template <typename W> __host__ __device__ constexpr int tw_per_chunk() { return (int)(16 / (2 * sizeof(W))); }
+
+// Load CH (1 or 2 for 32-bit words, 1 for 64-bit words) consecutive pairs
+// starting at index i (aligned to CH).
+template <typename W, int CH, int TWS>
+__device__ __forceinline__ void load_tw(const W *__restrict__ tw, uint32_t i, W (&z)[CH], W (&zp)[CH])
+{
+    constexpr int PC = tw_per_chunk<W>();
+    static_assert(CH <= PC, "one chunk at most");
+    if constexpr (TWS == TW_SMEM) {
+        const uint32_t c = tw_swz(i / PC);
+        if constexpr (sizeof(W) == 4 && CH == 2) {
+            uint4 q = reinterpret_cast<const uint4 *>(tw)[c];
+            z[0] = (W)q.x; zp[0] = (W)q.y; z[1] = (W)q.z; zp[1] = (W)q.w;
+        } else if constexpr (sizeof(W) == 4) {
+            uint2 q = reinterpret_cast<const uint2 *>(tw)[2 * c + (i & 1u)];
+            z[0] = (W)q.x; zp[0] = (W)q.y;
+        } else {
+            ulonglong2 q = reinterpret_cast<const ulonglong2 *>(tw)[c];
+            z[0] = (W)q.x; zp[0] = (W)q.y;
         }
-    } else if constexpr (sizeof(W) == 4) {
-        uint2 q = __ldg(reinterpret_cast<const uint2 *>(tw) + nb);
-        z[0] = (W)q.x; zp[0] = (W)q.y;
     } else {
-#pragma unroll
-        for (int t = 0; t < CNT; ++t) {
-            ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(tw) + nb + t);
-            z[t] = (W)q.x; zp[t] = (W)q.y;
+        if constexpr (sizeof(W) == 4 && CH == 2) {
+            uint4 q = __ldg(reinterpret_cast<const uint4 *>(tw) + (i >> 1));
+            z[0] = (W)q.x; zp[0] = (W)q.y; z[1] = (W)q.z; zp[1] = (W)q.w;
+        } else if constexpr (sizeof(W) == 4) {
+            uint2 q = __ldg(reinterpret_cast<const uint2 *>(tw) + i);
+            z[0] = (W)q.x; zp[0] = (W)q.y;
+        } else {
+            ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(tw) + i);
+            z[0] = (W)q.x; zp[0] = (W)q.y;
+        }
+    }
+}
+
+// Copy the first `pairs` entries of the plan's table into shared memory in
+// the swizzled layout (whole block cooperates; caller syncs afterwards).
+template <typename W>
+__device__ __forceinline__ void stage_twiddles(const W *__restrict__ tw, W *stw, uint32_t pairs)
+{
+    constexpr int PC = tw_per_chunk<W>();
+    const uint32_t chunks = (pairs + PC - 1) / PC;
+    for (uint32_t c = threadIdx.x; c < chunks; c += blockDim.x) {
+        if (PC == 2 && pairs == 1) {
+            reinterpret_cast<uint2 *>(stw)[0] = __ldg(reinterpret_cast<const uint2 *>(tw));
+        } else {
+            reinterpret_cast<uint4 *>(stw)[tw_swz(c)] = __ldg(reinterpret_cast<const uint4 *>(tw) + c);
         }
     }
 }
 
 // One forward level: element bit b = lo_P + JJ, global level L-1-b.
-template <typename W, int L, int LR, int P, int JJ, int NS>
+template <typename W, int L, int LR, int P, int JJ, int NS, int TWS>
 __device__ __forceinline__ void fwd_level(W (&v)[NS][Geo<W, LR>::R], uint32_t xbase,
                                           const W *__restrict__ tw, const ModC<W> &c)
 {
@@ -224,38 +268,44 @@ __device__ __forceinline__ void fwd_level(W (&v)[NS][Geo<W, LR>::R], uint32_t xb
         }
     } else {
         constexpr int CNT = R >> (JJ + 1);      // distinct nodes touched by this thread
-        W z[CNT], zp[CNT];
-        load_tw<W, CNT>(tw, xbase >> (b + 1), z, zp);
+        constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+        const uint32_t nb = xbase >> (b + 1);   // aligned to CNT
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (k & (1 << JJ)) continue;
-            const int t = k >> (JJ + 1);
+        for (int t0 = 0; t0 < CNT; t0 += CH) {
+            W z[CH], zp[CH];
+            load_tw<W, CH, TWS>(tw, nb + t0, z, zp);
 #pragma unroll
-            for (int s = 0; s < NS; ++s) ct_bfly<W>(v[s][k], v[s][k | (1 << JJ)], z[t], zp[t], c);
+            for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+                for (int j = 0; j < (1 << JJ); ++j) {
+                    const int k = ((t0 + tt) << (JJ + 1)) | j;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) ct_bfly<W>(v[s][k], v[s][k | (1 << JJ)], z[tt], zp[tt], c);
+                }
         }
     }
 }
 
 // Forward levels of pass P, highest element bit first.
-template <typename W, int L, int LR, int P, int JJ, int NS>
+template <typename W, int L, int LR, int P, int JJ, int NS, int TWS>
 __device__ __forceinline__ void fwd_levels(W (&v)[NS][Geo<W, LR>::R], uint32_t xbase,
                                            const W *__restrict__ tw, const ModC<W> &c)
 {
     if constexpr (JJ >= 0) {
-        fwd_level<W, L, LR, P, JJ, NS>(v, xbase, tw, c);
-        fwd_levels<W, L, LR, P, JJ - 1, NS>(v, xbase, tw, c);
+        fwd_level<W, L, LR, P, JJ, NS, TWS>(v, xbase, tw, c);
+        fwd_levels<W, L, LR, P, JJ - 1, NS, TWS>(v, xbase, tw, c);
     }
 }
 
-template <typename W, int L, int LR, int P, int NS>
+template <typename W, int L, int LR, int P, int NS, int TWS>
 __device__ __forceinline__ void fwd_pass(W (&v)[NS][Geo<W, LR>::R], uint32_t xbase,
                                          const W *__restrict__ tw, const ModC<W> &c)
 {
-    fwd_levels<W, L, LR, P, Geo<W, LR>::nb(P) - 1, NS>(v, xbase, tw, c);
+    fwd_levels<W, L, LR, P, Geo<W, LR>::nb(P) - 1, NS, TWS>(v, xbase, tw, c);
 }
 
 // One transposed (inverse-direction) level.
-template <typename W, int L, int LR, int P, int JJ>
+template <typename W, int L, int LR, int P, int JJ, int TWS>
 __device__ __forceinline__ void inv_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
                                           const W *__restrict__ tw, const ModC<W> &c)
 {
@@ -271,33 +321,108 @@ __device__ __forceinline__ void inv_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
         }
     } else {
         constexpr int CNT = R >> (JJ + 1);
-        W z[CNT], zp[CNT];
-        load_tw<W, CNT>(tw, xbase >> (b + 1), z, zp);
+        constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+        const uint32_t nb = xbase >> (b + 1);
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (k & (1 << JJ)) continue;
-            const int t = k >> (JJ + 1);
-            gs_bfly<W>(v[k], v[k | (1 << JJ)], z[t], zp[t], c);
+        for (int t0 = 0; t0 < CNT; t0 += CH) {
+            W z[CH], zp[CH];
+            load_tw<W, CH, TWS>(tw, nb + t0, z, zp);
+#pragma unroll
+            for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+                for (int j = 0; j < (1 << JJ); ++j) {
+                    const int k = ((t0 + tt) << (JJ + 1)) | j;
+                    gs_bfly<W>(v[k], v[k | (1 << JJ)], z[tt], zp[tt], c);
+                }
         }
     }
 }
 
 // Transposed levels of pass P, lowest element bit (deepest level) first.
-template <typename W, int L, int LR, int P, int JJ>
+template <typename W, int L, int LR, int P, int JJ, int TWS>
 __device__ __forceinline__ void inv_levels(W (&v)[Geo<W, LR>::R], uint32_t xbase,
                                            const W *__restrict__ tw, const ModC<W> &c)
 {
     if constexpr (JJ < Geo<W, LR>::nb(P)) {
-        inv_level<W, L, LR, P, JJ>(v, xbase, tw, c);
-        inv_levels<W, L, LR, P, JJ + 1>(v, xbase, tw, c);
+        inv_level<W, L, LR, P, JJ, TWS>(v, xbase, tw, c);
+        inv_levels<W, L, LR, P, JJ + 1, TWS>(v, xbase, tw, c);
     }
 }
 
-template <typename W, int L, int LR, int P>
+template <typename W, int L, int LR, int P, int TWS>
 __device__ __forceinline__ void inv_pass(W (&v)[Geo<W, LR>::R], uint32_t xbase,
                                          const W *__restrict__ tw, const ModC<W> &c)
 {
-    inv_levels<W, L, LR, P, 0>(v, xbase, tw, c);
+    inv_levels<W, L, LR, P, 0, TWS>(v, xbase, tw, c);
+}
+
+// ---- inverse direction, decimation in time -------------------------------
+//
+// The textbook iterative radix-2 algorithm of Sec. I, (a, b) -> (a + z b,
+// a - z b) over half-lengths 2^l = 1, 2, 4, ..., takes the bit-reversed
+// spectrum left by the forward tree to natural order and computes F applied
+// to it; F^{-1} = N^{-1} R F (Eq. 3) then needs the output index <-t>_N and
+// the factor N^-1.  Its twiddle for the pair (x, x + 2^l) is w^{(x mod 2^l)
+// N / 2^(l+1)} = z_{brv_l(x mod 2^l)}: the same table, read as one
+// contiguous run per thread and level.  Sums grow additively like the
+// forward ones, so no butterfly reduces: inputs < 2m leave the level l = 0
+// below 4m and every further level adds 2m.
+
+template <int J>
+__host__ __device__ constexpr int brv_c(int j)
+{
+    int r = 0;
+    for (int i = 0; i < J; ++i) r |= ((j >> i) & 1) << (J - 1 - i);
+    return r;
+}
+
+// Level l = lo_P + JJ of the inverse on one sequence.
+template <typename W, int LR, int P, int JJ, int TWS>
+__device__ __forceinline__ void dit_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
+                                          const W *__restrict__ tw, const ModC<W> &c)
+{
+    using G = Geo<W, LR>;
+    constexpr int R = G::R, lo = G::lo(P);
+    constexpr int l = lo + JJ;
+    if constexpr (l == 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (k & 1) continue;
+            W a0 = v[k];
+            v[k] = a0 + v[k + 1];
+            v[k + 1] = a0 - v[k + 1] + c.m2;
+        }
+    } else {
+        constexpr int CNT = 1 << JJ;                  // distinct twiddles of this level
+        constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+        uint32_t tlo = 0;
+        if constexpr (lo > 0) tlo = __brev(xbase & ((1u << lo) - 1u)) >> (32 - lo);
+        const uint32_t run = tlo << JJ;               // aligned to CNT
+#pragma unroll
+        for (int t0 = 0; t0 < CNT; t0 += CH) {
+            W z[CH], zp[CH];
+            load_tw<W, CH, TWS>(tw, run + t0, z, zp);
+#pragma unroll
+            for (int tt = 0; tt < CH; ++tt) {
+                const int j = brv_c<JJ>(t0 + tt);         // register bits below JJ
+#pragma unroll
+                for (int hi = 0; hi < (R >> (JJ + 1)); ++hi) {
+                    const int k = (hi << (JJ + 1)) | j;
+                    ct_bfly<W>(v[k], v[k | (1 << JJ)], z[tt], zp[tt], c);
+                }
+            }
+        }
+    }
+}
+
+template <typename W, int LR, int P, int JJ, int TWS>
+__device__ __forceinline__ void dit_levels(W (&v)[Geo<W, LR>::R], uint32_t xbase,
+                                           const W *__restrict__ tw, const ModC<W> &c)
+{
+    if constexpr (JJ < Geo<W, LR>::nb(P)) {
+        dit_level<W, LR, P, JJ, TWS>(v, xbase, tw, c);
+        dit_levels<W, LR, P, JJ + 1, TWS>(v, xbase, tw, c);
+    }
 }
 
 // Store the registers of NS sequences in the layout of pass P into the
@@ -324,15 +449,15 @@ __device__ __forceinline__ void exchange(W (&v)[NS][Geo<W, LR>::R], W *S, uint32
 }
 
 // All forward passes P = FROM .. NPASS-1 (registers start in layout FROM).
-template <typename W, int L, int LR, int P, int NS>
+template <typename W, int L, int LR, int P, int NS, int TWS>
 __device__ __forceinline__ void fwd_all(W (&v)[NS][Geo<W, LR>::R], uint32_t rowoff, uint32_t tau,
                                         W *S, int gid, const W *__restrict__ tw, const ModC<W> &c)
 {
     using G = Geo<W, LR>;
-    fwd_pass<W, L, LR, P, NS>(v, rowoff + G::base(P, tau), tw, c);
+    fwd_pass<W, L, LR, P, NS, TWS>(v, rowoff + G::base(P, tau), tw, c);
     if constexpr (P + 1 < G::NPASS) {
         exchange<W, LR, P, P + 1, NS>(v, S, tau, gid);
-        fwd_all<W, L, LR, P + 1, NS>(v, rowoff, tau, S, gid, tw, c);
+        fwd_all<W, L, LR, P + 1, NS, TWS>(v, rowoff, tau, S, gid, tw, c);
     }
 }
 
@@ -353,16 +478,34 @@ __device__ __forceinline__ void exchange1(W (&v)[Geo<W, LR>::R], W *S, uint32_t 
 }
 
 // All inverse passes P = FROM .. 0 (registers start in layout FROM).
-template <typename W, int L, int LR, int P>
+template <typename W, int L, int LR, int P, int TWS>
 __device__ __forceinline__ void inv_all(W (&v)[Geo<W, LR>::R], uint32_t rowoff, uint32_t tau,
                                         W *S, int gid, const W *__restrict__ tw, const ModC<W> &c)
 {
     using G = Geo<W, LR>;
-    inv_pass<W, L, LR, P>(v, rowoff + G::base(P, tau), tw, c);
+    inv_pass<W, L, LR, P, TWS>(v, rowoff + G::base(P, tau), tw, c);
     if constexpr (P > 0) {
         exchange1<W, LR, P, P - 1>(v, S, tau, gid);
-        inv_all<W, L, LR, P - 1>(v, rowoff, tau, S, gid, tw, c);
+        inv_all<W, L, LR, P - 1, TWS>(v, rowoff, tau, S, gid, tw, c);
     }
 }
+
+// All inverse passes, decimation in time, P = FROM .. 0.
+template <typename W, int LR, int P, int TWS>
+__device__ __forceinline__ void dit_all(W (&v)[Geo<W, LR>::R], uint32_t rowoff, uint32_t tau,
+                                        W *S, int gid, const W *__restrict__ tw, const ModC<W> &c)
+{
+    using G = Geo<W, LR>;
+    dit_levels<W, LR, P, 0, TWS>(v, rowoff + G::base(P, tau), tw, c);
+    if constexpr (P > 0) {
+        exchange1<W, LR, P, P - 1>(v, S, tau, gid);
+        dit_all<W, LR, P - 1, TWS>(v, rowoff, tau, S, gid, tw, c);
+    }
+}
+
+// Final canonical residue of a lazily bounded value: Shoup product by the
+// factor (z, zp) (1 or N^-1) into [0, 2m), then one conditional subtraction.
+template <typename W>
+__device__ __forceinline__ W canon(W v, W z, W zp, W m) { return csub<W>(shoup<W>(v, z, zp, m), m); }
 
 }  // namespace ntt

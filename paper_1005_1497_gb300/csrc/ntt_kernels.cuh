@@ -34,6 +34,13 @@ template <typename W> struct RowArgs {
     ModC<W> c;
 };
 
+// Shared-memory copy of the twiddle table of a whole-sequence kernel (N/2 pairs).
+template <typename W, int L>
+struct TwBytes {
+    static constexpr uint32_t pairs = L >= 1 ? (1u << (L - 1)) : 1u;
+    static constexpr size_t v = ((size_t)pairs * 2 * sizeof(W) + 15) / 16 * 16;
+};
+
 template <typename W, int L, int LR>
 struct RowShape {
     using G = Geo<W, LR>;
@@ -83,11 +90,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_rows(RowArgs<W> a)
             v[0][k] = fp[b0 + ((uint32_t)k << lo0)];
             v[1][k] = gp[b0 + ((uint32_t)k << lo0)];
         }
-        fwd_all<W, L, LR, 0, 2>(v, rowoff, tau, S, gid, a.tw, a.c);
+        fwd_all<W, L, LR, 0, 2, TW_GLOBAL>(v, rowoff, tau, S, gid, a.tw, a.c);
         W hv[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) hv[k] = pointwise(v[0][k], v[1][k], a.c);
-        inv_all<W, L, LR, G::NPASS - 1>(hv, rowoff, tau, S, gid, a.tw, a.c);
+        inv_all<W, L, LR, G::NPASS - 1, TW_GLOBAL>(hv, rowoff, tau, S, gid, a.tw, a.c);
         if constexpr (FULL) {
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -98,6 +105,299 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_rows(RowArgs<W> a)
 #pragma unroll
             for (int k = 0; k < R; ++k) hp[b0 + ((uint32_t)k << lo0)] = hv[k];
         }
+    }
+}
+
+// Asynchronous 4- or 8-byte global-to-shared copy (cp.async), and the wait
+// for all of this thread's outstanding copies.
+template <typename W>
+__device__ __forceinline__ void cp_async_word(W *smem_dst, const W *gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"((int)sizeof(W)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Hint: fetch `bytes` bytes at p into L2 with one bulk copy-engine
+// request (no registers, no shared memory).  Skipped unless 16-byte aligned.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    if (((uintptr_t)p & 15u) == 0 && bytes >= 16)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
+}
+
+// Fused convolution of whole sequences (L <= LR_max), persistent.  The block
+// stages the twiddle table in shared memory once.  Per pair, f and g are
+// transformed together (one set of twiddle reads serves both) through shared
+// regions 0 and 1, multiplied pointwise, and sent back through region 0 by
+// the decimation-in-time inverse; results are stored canonical at <-x>_N.
+// At the start of each pair one thread asks the copy engine to bring the
+// next pair's f and g into L2, so their loads do not wait on HBM.
+template <typename W, int L, int SRC>
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
+{
+    using G = Geo<W, L>;
+    constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, L>::GPC;
+    constexpr uint32_t N = 1u << L;
+    constexpr int last = G::NPASS - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gid = threadIdx.x / T;
+    const uint32_t tau = threadIdx.x % T;
+    W *stw = reinterpret_cast<W *>(smem_raw);
+    W *S = reinterpret_cast<W *>(smem_raw + TwBytes<W, L>::v) + (size_t)gid * 2 * G::ROWP;
+    const uint32_t b0 = G::base(0, tau);
+    constexpr int lo0 = G::lo(0);
+    stage_twiddles<W>(a.tw, stw, TwBytes<W, L>::pairs);
+    __syncthreads();
+
+    auto ptrs = [&](long long rho, const W *&fp, const W *&gp, W *&hp) {
+        const long long pair = a.pair0 + rho;
+        if constexpr (SRC == 1) {
+            const DevDesc<W> d = a.descs[pair];
+            fp = d.f; gp = d.g; hp = d.h;
+        } else {
+            fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
+        }
+    };
+    const long long stride = (long long)gridDim.x * GPC;
+    for (long long rho = (long long)blockIdx.x * GPC + gid; rho < a.nrows; rho += stride) {
+        const W *fp, *gp;
+        W *hp;
+        ptrs(rho, fp, gp, hp);
+        if (tau == 0 && rho + stride < a.nrows) {
+            const W *fn, *gn;
+            W *hn;
+            ptrs(rho + stride, fn, gn, hn);
+            prefetch_l2(fn, N * (uint32_t)sizeof(W));
+            prefetch_l2(gn, N * (uint32_t)sizeof(W));
+        }
+        W v[2][R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            v[0][k] = fp[b0 + ((uint32_t)k << lo0)];
+            v[1][k] = gp[b0 + ((uint32_t)k << lo0)];
+        }
+        fwd_all<W, L, L, 0, 2, TW_SMEM>(v, 0u, tau, S, gid, stw, a.c);
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[0][k], v[1][k], a.c);
+        dit_all<W, L, last, TW_SMEM>(v[0], 0u, tau, S, gid, stw, a.c);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t x = b0 + ((uint32_t)k << lo0);
+            hp[(N - x) & (N - 1u)] = canon<W>(v[0][k], (W)1, a.c.onep, a.c.m);
+        }
+    }
+}
+
+// ---- column/row fused kernel ---------------------------------------------
+//
+// For 2^RW < N <= 2^LR_max (RW = log2 of the 32 x R elements one warp holds:
+// 10 for 32-bit words), the index splits into LC = L - RW top bits and RW low
+// bits.  The forward tree's first LC levels act on "columns" (fixed low bits,
+// 2^LC elements each): each thread holds whole columns in registers, whose
+// node twiddles are the first 2^LC - 1 table entries for every column.  One
+// block-wide transpose through shared memory then gives every warp a
+// contiguous "row" of 2^RW elements, whose remaining levels (and the first
+// RW levels of the inverse) need only warp-level exchanges, so warps run
+// independently and one warp's exchanges overlap another's arithmetic.  The
+// inverse's last LC levels act on columns again; their twiddles are the runs
+// z_{brv_RW(c) 2^J + t}.  Shared memory holds, per row, the f and g slices
+// side by side (stride ROWP of the row geometry).
+
+// Forward node levels of one column of RC = 2^LC elements stored at v[OFF ..].
+template <typename W, int LC, int OFF, int J, int TWS, int RR>
+__device__ __forceinline__ void colf_levels(W (&v)[RR], const W *__restrict__ tw, const ModC<W> &c, bool top)
+{
+    if constexpr (J >= 0) {
+        constexpr int RC = 1 << LC;
+        constexpr int dg = LC - 1 - J;
+        if constexpr (dg == 0) {
+            // level 0 of the whole tree when the columns hold the top bits
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                if (k & (1 << J)) continue;
+                if (top) ct_bfly_one<W>(v[OFF + k], v[OFF + (k | (1 << J))], c);
+            }
+        } else {
+            constexpr int CNT = RC >> (J + 1);
+            constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+#pragma unroll
+            for (int t0 = 0; t0 < CNT; t0 += CH) {
+                W z[CH], zp[CH];
+                load_tw<W, CH, TWS>(tw, (uint32_t)t0, z, zp);
+#pragma unroll
+                for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+                    for (int j = 0; j < (1 << J); ++j) {
+                        const int k = ((t0 + tt) << (J + 1)) | j;
+                        ct_bfly<W>(v[OFF + k], v[OFF + (k | (1 << J))], z[tt], zp[tt], c);
+                    }
+            }
+        }
+        colf_levels<W, LC, OFF, J - 1, TWS, RR>(v, tw, c, top);
+    }
+}
+
+// Inverse (decimation-in-time) levels l = RW + J of one column c, tlo = brv_RW(c).
+template <typename W, int LC, int OFF, int J, int TWS, int RR>
+__device__ __forceinline__ void cold_levels(W (&v)[RR], uint32_t tlo, const W *__restrict__ tw, const ModC<W> &c)
+{
+    if constexpr (J < LC) {
+        constexpr int RC = 1 << LC;
+        constexpr int CNT = 1 << J;
+        constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+        const uint32_t run = tlo << J;
+#pragma unroll
+        for (int t0 = 0; t0 < CNT; t0 += CH) {
+            W z[CH], zp[CH];
+            load_tw<W, CH, TWS>(tw, run + t0, z, zp);
+#pragma unroll
+            for (int tt = 0; tt < CH; ++tt) {
+                const int j = brv_c<J>(t0 + tt);
+#pragma unroll
+                for (int hi = 0; hi < (RC >> (J + 1)); ++hi) {
+                    const int k = (hi << (J + 1)) | j;
+                    ct_bfly<W>(v[OFF + k], v[OFF + (k | (1 << J))], z[tt], zp[tt], c);
+                }
+            }
+        }
+        cold_levels<W, LC, OFF, J + 1, TWS, RR>(v, tlo, tw, c);
+    }
+}
+
+// All columns JC .. CPT-1 held by a thread (column j at v[j * 2^LC ..]).
+template <typename W, int LC, int JC, int CPT, int TWS, int RR>
+__device__ __forceinline__ void colf_all(W (&v)[RR], const W *__restrict__ tw, const ModC<W> &c)
+{
+    if constexpr (JC < CPT) {
+        colf_levels<W, LC, JC * (1 << LC), LC - 1, TWS, RR>(v, tw, c, true);
+        colf_all<W, LC, JC + 1, CPT, TWS, RR>(v, tw, c);
+    }
+}
+
+template <typename W, int LC, int RW, int JC, int CPT, int TPP, int TWS, int RR>
+__device__ __forceinline__ void cold_all(W (&v)[RR], uint32_t ptau, const W *__restrict__ tw, const ModC<W> &c)
+{
+    if constexpr (JC < CPT) {
+        const uint32_t col = ptau + (uint32_t)JC * TPP;
+        cold_levels<W, LC, JC * (1 << LC), 0, TWS, RR>(v, __brev(col) >> (32 - RW), tw, c);
+        cold_all<W, LC, RW, JC + 1, CPT, TPP, TWS, RR>(v, ptau, tw, c);
+    }
+}
+
+template <typename W, int L>
+struct CRShape {
+    static constexpr int RW = Arith<W>::RB + 5;
+    static constexpr int LC = L - RW;
+    static constexpr int RC = 1 << LC;
+    using GR = Geo<W, RW>;
+    static constexpr int TPP = 32 * RC;                     // threads per pair
+    static constexpr int PPC = BLOCK / TPP;                 // pairs per block
+    static constexpr int CPT = (1 << RW) / TPP;             // columns per thread
+    static constexpr size_t smem = TwBytes<W, L>::v + (size_t)PPC * RC * 2 * GR::ROWP * sizeof(W);
+};
+
+template <typename W, int L, int SRC>
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
+{
+    using SH = CRShape<W, L>;
+    using GR = typename SH::GR;
+    constexpr int RW = SH::RW, LC = SH::LC, RC = SH::RC, TPP = SH::TPP, PPC = SH::PPC, CPT = SH::CPT;
+    constexpr int R = GR::R;
+    static_assert(LC >= 1 && CPT * RC == R, "column/row split");
+    constexpr uint32_t N = 1u << L;
+    constexpr int last = GR::NPASS - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int pid = threadIdx.x / TPP;
+    const uint32_t ptau = threadIdx.x % TPP;
+    const int wr = (int)(ptau >> 5);
+    const uint32_t lane = ptau & 31u;
+    W *stw = reinterpret_cast<W *>(smem_raw);
+    W *P = reinterpret_cast<W *>(smem_raw + TwBytes<W, L>::v) + (size_t)pid * RC * 2 * GR::ROWP;
+    W *Srow = P + (size_t)wr * 2 * GR::ROWP;                // this warp's f slice; g slice follows
+    const uint32_t b0 = GR::base(0, lane);
+    constexpr int lo0 = GR::lo(0);
+    stage_twiddles<W>(a.tw, stw, TwBytes<W, L>::pairs);
+    __syncthreads();
+
+    auto psync = [&]() {
+        if constexpr (TPP == BLOCK) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(pid + 1), "r"(TPP) : "memory");
+    };
+    auto ptrs = [&](long long rho, const W *&fp, const W *&gp, W *&hp) {
+        const long long pair = a.pair0 + rho;
+        if constexpr (SRC == 1) {
+            const DevDesc<W> d = a.descs[pair];
+            fp = d.f; gp = d.g; hp = d.h;
+        } else {
+            fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
+        }
+    };
+    const long long stride = (long long)gridDim.x * PPC;
+    for (long long rho = (long long)blockIdx.x * PPC + pid; rho < a.nrows; rho += stride) {
+        const W *fp, *gp;
+        W *hp;
+        ptrs(rho, fp, gp, hp);
+        if (ptau == 0 && rho + stride < a.nrows) {
+            const W *fn, *gn;
+            W *hn;
+            ptrs(rho + stride, fn, gn, hn);
+            prefetch_l2(fn, N * (uint32_t)sizeof(W));
+            prefetch_l2(gn, N * (uint32_t)sizeof(W));
+        }
+        // forward, column phase: columns c = ptau + j TPP, elements x = c + k 2^RW
+        W v[2][R];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
+                v[0][j * RC + k] = fp[x];
+                v[1][j * RC + k] = gp[x];
+            }
+        colf_all<W, LC, 0, CPT, TW_SMEM, R>(v[0], stw, a.c);
+        colf_all<W, LC, 0, CPT, TW_SMEM, R>(v[1], stw, a.c);
+        psync();                                            // slices free (previous pair)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const uint32_t y = ptau + (uint32_t)j * TPP;
+                P[(size_t)k * 2 * GR::ROWP + GR::pad(y)] = v[0][j * RC + k];
+                P[(size_t)k * 2 * GR::ROWP + GR::ROWP + GR::pad(y)] = v[1][j * RC + k];
+            }
+        psync();
+        // forward, row phase (warp wr owns row wr)
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t y = b0 + ((uint32_t)k << lo0);
+            v[0][k] = Srow[GR::pad(y)];
+            v[1][k] = Srow[GR::ROWP + GR::pad(y)];
+        }
+        fwd_all<W, L, RW, 0, 2, TW_SMEM>(v, (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[0][k], v[1][k], a.c);
+        // inverse, row phase
+        dit_all<W, RW, last, TW_SMEM>(v[0], (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
+#pragma unroll
+        for (int k = 0; k < R; ++k) Srow[GR::pad(b0 + ((uint32_t)k << lo0))] = v[0][k];
+        psync();
+        // inverse, column phase, and the output at <-x>_N
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const uint32_t col = ptau + (uint32_t)j * TPP;
+#pragma unroll
+            for (int k = 0; k < RC; ++k) v[0][j * RC + k] = P[(size_t)k * 2 * GR::ROWP + GR::pad(col)];
+        }
+        cold_all<W, LC, RW, 0, CPT, TPP, TW_SMEM, R>(v[0], ptau, stw, a.c);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
+                hp[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
+            }
     }
 }
 
@@ -123,9 +423,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(NttArgs<W> a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gid = threadIdx.x / T;
     const uint32_t tau = threadIdx.x % T;
-    W *S = reinterpret_cast<W *>(smem_raw) + (size_t)gid * G::ROWP;
+    W *stw = reinterpret_cast<W *>(smem_raw);
+    W *S = reinterpret_cast<W *>(smem_raw + TwBytes<W, L>::v) + (size_t)gid * G::ROWP;
     const uint32_t b0 = G::base(0, tau), bl = G::base(last, tau);
     constexpr int lo0 = G::lo(0), lol = G::lo(last);
+    stage_twiddles<W>(a.tw, stw, TwBytes<W, L>::pairs);
+    __syncthreads();
     const W scale = INV ? a.c.ninv : (W)1;
     const W scalep = INV ? a.c.ninvp : a.c.onep;
 
@@ -135,7 +438,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(NttArgs<W> a)
         W v[1][R];
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = xp[b0 + ((uint32_t)k << lo0)];
-        fwd_all<W, L, L, 0, 1>(v, 0u, tau, S, gid, a.tw, a.c);
+        fwd_all<W, L, L, 0, 1, TW_SMEM>(v, 0u, tau, S, gid, stw, a.c);
         group_sync<T>(gid);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -170,6 +473,18 @@ template <typename W> struct ColArgs {
     ModC<W> c;
 };
 
+// Pairs 0 .. CNT-1 of the plan's table (the same for every column).
+template <typename W, int CNT>
+__device__ __forceinline__ void load_tw_run(const W *__restrict__ tw, W (&z)[CNT], W (&zp)[CNT])
+{
+#pragma unroll
+    for (int t = 0; t < CNT; ++t) {
+        W a[1], ap[1];
+        load_tw<W, 1, TW_GLOBAL>(tw, (uint32_t)t, a, ap);
+        z[t] = a[0]; zp[t] = ap[0];
+    }
+}
+
 template <typename W, int L, int LR, int J>
 __device__ __forceinline__ void col_fwd_level(W (&v)[1 << (L - LR)], const W *__restrict__ tw, const ModC<W> &c)
 {
@@ -185,7 +500,7 @@ __device__ __forceinline__ void col_fwd_level(W (&v)[1 << (L - LR)], const W *__
     } else {
         constexpr int CNT = RC >> (J + 1);
         W z[CNT], zp[CNT];
-        load_tw<W, CNT>(tw, 0u, z, zp);
+        load_tw_run<W, CNT>(tw, z, zp);
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             if (k & (1 << J)) continue;
@@ -218,7 +533,7 @@ __device__ __forceinline__ void col_inv_levels(W (&v)[1 << (L - LR)], const W *_
         } else {
             constexpr int CNT = RC >> (J + 1);
             W z[CNT], zp[CNT];
-            load_tw<W, CNT>(tw, 0u, z, zp);
+            load_tw_run<W, CNT>(tw, z, zp);
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 if (k & (1 << J)) continue;
@@ -303,7 +618,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_rows_fwd(RowArgs<W> a)
         W v[1][R];
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = p[b0 + ((uint32_t)k << G::lo(0))];
-        fwd_all<W, L, LR, 0, 1>(v, row << LR, tau, S, gid, a.tw, a.c);
+        fwd_all<W, L, LR, 0, 1, TW_GLOBAL>(v, row << LR, tau, S, gid, a.tw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) p[bl + ((uint32_t)k << G::lo(last))] = v[0][k];
     }

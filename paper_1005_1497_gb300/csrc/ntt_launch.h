@@ -12,6 +12,8 @@ template <typename W> struct Launch {
     static constexpr int LMAX = LRMAX + 5;     // split path: up to 5 column bits
     // rows transformed concurrently by one block of the row kernels
     static int rows_per_block(int LR);
+    // pairs in flight per block of the whole-sequence fused kernels
+    static int pairs_per_block(int L);
     // whole-sequence fused convolution (L <= LRMAX); src 0 = contiguous, 1 = descriptors
     static cudaError_t conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st);
     // split path pieces (LRMAX < L <= LMAX)
