@@ -35,9 +35,9 @@ static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t 
         return cudaGetLastError();
     } else if constexpr (L <= LRMax<W>::v) {
         constexpr size_t smem = CRShape<W, L>::smem;
-        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, SRC>, smem);
+        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, L, SRC>, smem);
         if (init != cudaSuccess) return init;
-        k_conv_cr<W, L, SRC><<<grid, BLOCK, smem, st>>>(a);
+        k_conv_cr<W, L, L, SRC><<<grid, BLOCK, smem, st>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
@@ -57,10 +57,10 @@ static cudaError_t launch_conv_split(const RowArgs<W> &a, int grid, cudaStream_t
 {
     constexpr int LR = LRMax<W>::v;
     if constexpr (L > LR && L <= LR + 5) {
-        constexpr size_t smem = RowShape<W, L, LR>::smem(2);
-        static const cudaError_t init = ensure_smem(k_conv_rows<W, L, LR, 0>, smem);
+        constexpr size_t smem = CRShape<W, L, LR>::smem;
+        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, LR, 0>, smem);
         if (init != cudaSuccess) return init;
-        k_conv_rows<W, L, LR, 0><<<grid, BLOCK, smem, st>>>(a);
+        k_conv_cr<W, L, LR, 0><<<grid, BLOCK, smem, st>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;

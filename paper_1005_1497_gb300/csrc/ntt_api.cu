@@ -242,7 +242,7 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);
         RowArgs<W> ra{scratch, scratch + (size_t)wave * N, scratch, nullptr, rows, 0, tw, c};
-        e = Launch<W>::conv_rows_split(p->L, ra, row_grid(p->nsm, rows, Launch<W>::rows_per_block(p->LR)), st);
+        e = Launch<W>::conv_rows_split(p->L, ra, row_grid(p->nsm, rows, Launch<W>::pairs_per_block(p->LR)), st);
         if (e != cudaSuccess) return e;
         e = Launch<W>::cols_inv(p->L, mode, ca, st);
         if (e != cudaSuccess) return e;

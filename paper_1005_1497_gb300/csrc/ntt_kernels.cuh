@@ -48,77 +48,6 @@ struct RowShape {
     static constexpr size_t smem(int ns) { return (size_t)GPC * ns * G::ROWP * sizeof(W); }
 };
 
-// Fused convolution rows: forward transforms of f and g, pointwise product
-// with N^-1, transposed transform back, all in registers and shared memory.
-template <typename W, int L, int LR, int SRC>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_rows(RowArgs<W> a)
-{
-    using G = Geo<W, LR>;
-    constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, LR>::GPC;
-    constexpr bool FULL = (L == LR);
-    constexpr uint32_t N = 1u << L;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int gid = threadIdx.x / T;
-    const uint32_t tau = threadIdx.x % T;
-    W *S = reinterpret_cast<W *>(smem_raw) + (size_t)gid * 2 * G::ROWP;
-    const uint32_t b0 = G::base(0, tau);
-    constexpr int lo0 = G::lo(0);
-
-    for (long long rho = (long long)blockIdx.x * GPC + gid; rho < a.nrows; rho += (long long)gridDim.x * GPC) {
-        const W *fp, *gp;
-        W *hp;
-        uint32_t rowoff;
-        if constexpr (FULL) {
-            const long long pair = a.pair0 + rho;
-            if constexpr (SRC == 1) {
-                const DevDesc<W> d = a.descs[pair];
-                fp = d.f; gp = d.g; hp = d.h;
-            } else {
-                fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
-            }
-            rowoff = 0;
-        } else {
-            const long long pw = rho >> (L - LR);
-            const uint32_t row = (uint32_t)rho & ((1u << (L - LR)) - 1u);
-            const size_t off = (size_t)pw * N + ((size_t)row << LR);
-            fp = a.f + off; gp = a.g + off; hp = a.h + off;
-            rowoff = row << LR;
-        }
-        W v[2][R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            v[0][k] = fp[b0 + ((uint32_t)k << lo0)];
-            v[1][k] = gp[b0 + ((uint32_t)k << lo0)];
-        }
-        fwd_all<W, L, LR, 0, 2, TW_GLOBAL>(v, rowoff, tau, S, gid, a.tw, a.c);
-        W hv[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) hv[k] = pointwise(v[0][k], v[1][k], a.c);
-        inv_all<W, L, LR, G::NPASS - 1, TW_GLOBAL>(hv, rowoff, tau, S, gid, a.tw, a.c);
-        if constexpr (FULL) {
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const uint32_t x = b0 + ((uint32_t)k << lo0);
-                hp[(N - x) & (N - 1u)] = csub<W>(hv[k], a.c.m);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < R; ++k) hp[b0 + ((uint32_t)k << lo0)] = hv[k];
-        }
-    }
-}
-
-// Asynchronous 4- or 8-byte global-to-shared copy (cp.async), and the wait
-// for all of this thread's outstanding copies.
-template <typename W>
-__device__ __forceinline__ void cp_async_word(W *smem_dst, const W *gmem_src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"((int)sizeof(W)) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // Hint: fetch `bytes` bytes at p into L2 with one bulk copy-engine
 // request (no registers, no shared memory).  Skipped unless 16-byte aligned.
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
@@ -206,26 +135,31 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
 // side by side (stride ROWP of the row geometry).
 
 // Forward node levels of one column of RC = 2^LC elements stored at v[OFF ..].
-template <typename W, int LC, int OFF, int J, int TWS, int RR>
-__device__ __forceinline__ void colf_levels(W (&v)[RR], const W *__restrict__ tw, const ModC<W> &c, bool top)
+// The column's top bit sits at global level DG0 (0 when the columns hold the
+// top bits of the whole transform); node indices at the level of register
+// bit J are nbase_J + (k >> (J + 1)), with nbase_J = rowbase >> (J + 1) for
+// a row that is itself part of a longer transform (rowbase = its global
+// index offset divided by 2^RW).
+template <typename W, int LC, int OFF, int J, int DG0, int TWS, int RR>
+__device__ __forceinline__ void colf_levels(W (&v)[RR], uint32_t rowbase, const W *__restrict__ tw, const ModC<W> &c)
 {
     if constexpr (J >= 0) {
         constexpr int RC = 1 << LC;
-        constexpr int dg = LC - 1 - J;
+        constexpr int dg = DG0 + LC - 1 - J;
         if constexpr (dg == 0) {
-            // level 0 of the whole tree when the columns hold the top bits
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 if (k & (1 << J)) continue;
-                if (top) ct_bfly_one<W>(v[OFF + k], v[OFF + (k | (1 << J))], c);
+                ct_bfly_one<W>(v[OFF + k], v[OFF + (k | (1 << J))], c);
             }
         } else {
             constexpr int CNT = RC >> (J + 1);
             constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+            const uint32_t nbase = rowbase >> (J + 1);
 #pragma unroll
             for (int t0 = 0; t0 < CNT; t0 += CH) {
                 W z[CH], zp[CH];
-                load_tw<W, CH, TWS>(tw, (uint32_t)t0, z, zp);
+                load_tw<W, CH, TWS>(tw, nbase + (uint32_t)t0, z, zp);
 #pragma unroll
                 for (int tt = 0; tt < CH; ++tt)
 #pragma unroll
@@ -235,7 +169,52 @@ __device__ __forceinline__ void colf_levels(W (&v)[RR], const W *__restrict__ tw
                     }
             }
         }
-        colf_levels<W, LC, OFF, J - 1, TWS, RR>(v, tw, c, top);
+        colf_levels<W, LC, OFF, J - 1, DG0, TWS, RR>(v, rowbase, tw, c);
+    }
+}
+
+// Transposed (inverse-direction) node levels of one column, deepest first:
+// the exact reverse of colf_levels with the same twiddles.  Inputs < 2m,
+// outputs < 2m.
+template <typename W, int LC, int OFF, int J, int DG0, int TWS, int RR>
+__device__ __forceinline__ void colg_levels(W (&v)[RR], uint32_t rowbase, const W *__restrict__ tw, const ModC<W> &c)
+{
+    if constexpr (J < LC) {
+        constexpr int RC = 1 << LC;
+        constexpr int dg = DG0 + LC - 1 - J;
+        if constexpr (dg == 0) {
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                if (k & (1 << J)) continue;
+                gs_bfly_one<W>(v[OFF + k], v[OFF + (k | (1 << J))], c);
+            }
+        } else {
+            constexpr int CNT = RC >> (J + 1);
+            constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+            const uint32_t nbase = rowbase >> (J + 1);
+#pragma unroll
+            for (int t0 = 0; t0 < CNT; t0 += CH) {
+                W z[CH], zp[CH];
+                load_tw<W, CH, TWS>(tw, nbase + (uint32_t)t0, z, zp);
+#pragma unroll
+                for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+                    for (int j = 0; j < (1 << J); ++j) {
+                        const int k = ((t0 + tt) << (J + 1)) | j;
+                        gs_bfly<W>(v[OFF + k], v[OFF + (k | (1 << J))], z[tt], zp[tt], c);
+                    }
+            }
+        }
+        colg_levels<W, LC, OFF, J + 1, DG0, TWS, RR>(v, rowbase, tw, c);
+    }
+}
+
+template <typename W, int LC, int JC, int CPT, int DG0, int TWS, int RR>
+__device__ __forceinline__ void colg_all(W (&v)[RR], uint32_t rowbase, const W *__restrict__ tw, const ModC<W> &c)
+{
+    if constexpr (JC < CPT) {
+        colg_levels<W, LC, JC * (1 << LC), 0, DG0, TWS, RR>(v, rowbase, tw, c);
+        colg_all<W, LC, JC + 1, CPT, DG0, TWS, RR>(v, rowbase, tw, c);
     }
 }
 
@@ -267,12 +246,12 @@ __device__ __forceinline__ void cold_levels(W (&v)[RR], uint32_t tlo, const W *_
 }
 
 // All columns JC .. CPT-1 held by a thread (column j at v[j * 2^LC ..]).
-template <typename W, int LC, int JC, int CPT, int TWS, int RR>
-__device__ __forceinline__ void colf_all(W (&v)[RR], const W *__restrict__ tw, const ModC<W> &c)
+template <typename W, int LC, int JC, int CPT, int DG0, int TWS, int RR>
+__device__ __forceinline__ void colf_all(W (&v)[RR], uint32_t rowbase, const W *__restrict__ tw, const ModC<W> &c)
 {
     if constexpr (JC < CPT) {
-        colf_levels<W, LC, JC * (1 << LC), LC - 1, TWS, RR>(v, tw, c, true);
-        colf_all<W, LC, JC + 1, CPT, TWS, RR>(v, tw, c);
+        colf_levels<W, LC, JC * (1 << LC), LC - 1, DG0, TWS, RR>(v, rowbase, tw, c);
+        colf_all<W, LC, JC + 1, CPT, DG0, TWS, RR>(v, rowbase, tw, c);
     }
 }
 
@@ -286,26 +265,37 @@ __device__ __forceinline__ void cold_all(W (&v)[RR], uint32_t ptau, const W *__r
     }
 }
 
-template <typename W, int L>
+template <typename W, int L, int LROW = L>
 struct CRShape {
     static constexpr int RW = Arith<W>::RB + 5;
-    static constexpr int LC = L - RW;
+    static constexpr int LC = LROW - RW;                    // column bits inside one row
     static constexpr int RC = 1 << LC;
     using GR = Geo<W, RW>;
-    static constexpr int TPP = 32 * RC;                     // threads per pair
-    static constexpr int PPC = BLOCK / TPP;                 // pairs per block
+    static constexpr int TPP = 32 * RC;                     // threads per row
+    static constexpr int PPC = BLOCK / TPP;                 // rows per block
     static constexpr int CPT = (1 << RW) / TPP;             // columns per thread
-    static constexpr size_t smem = TwBytes<W, L>::v + (size_t)PPC * RC * 2 * GR::ROWP * sizeof(W);
+    // shared twiddles: the whole table (whole sequences) or only the entries
+    // below 2^(LROW-1) that the inverse levels inside a row read (split rows)
+    static constexpr int TWL = (L == LROW) ? L : 0;         // split rows read the plan's table
+    static constexpr size_t smem = TwBytes<W, TWL>::v + (size_t)PPC * RC * 2 * GR::ROWP * sizeof(W);
 };
 
-template <typename W, int L, int SRC>
+// Column/row fused convolution.  L == LROW: whole sequences (f, g, h or the
+// descriptor list; output canonical at <-x>_N).  L > LROW: one row of 2^LROW
+// elements of the split path per row group, inputs F~, G~ and output H~ in
+// the wave's scratch; the forward node twiddles of such a row depend on the
+// row and are read from the plan's table, the inverse ones do not and are
+// read from shared memory.
+template <typename W, int L, int LROW, int SRC>
 __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
 {
-    using SH = CRShape<W, L>;
+    using SH = CRShape<W, L, LROW>;
     using GR = typename SH::GR;
     constexpr int RW = SH::RW, LC = SH::LC, RC = SH::RC, TPP = SH::TPP, PPC = SH::PPC, CPT = SH::CPT;
     constexpr int R = GR::R;
     static_assert(LC >= 1 && CPT * RC == R, "column/row split");
+    constexpr bool FULL = (L == LROW);
+    constexpr int FTW = FULL ? TW_SMEM : TW_GLOBAL;         // forward twiddle source
     constexpr uint32_t N = 1u << L;
     constexpr int last = GR::NPASS - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -314,37 +304,51 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
     const int wr = (int)(ptau >> 5);
     const uint32_t lane = ptau & 31u;
     W *stw = reinterpret_cast<W *>(smem_raw);
-    W *P = reinterpret_cast<W *>(smem_raw + TwBytes<W, L>::v) + (size_t)pid * RC * 2 * GR::ROWP;
+    W *P = reinterpret_cast<W *>(smem_raw + TwBytes<W, SH::TWL>::v) + (size_t)pid * RC * 2 * GR::ROWP;
     W *Srow = P + (size_t)wr * 2 * GR::ROWP;                // this warp's f slice; g slice follows
+    const W *ftw = FULL ? stw : a.tw;
     const uint32_t b0 = GR::base(0, lane);
     constexpr int lo0 = GR::lo(0);
-    stage_twiddles<W>(a.tw, stw, TwBytes<W, L>::pairs);
-    __syncthreads();
+    if constexpr (FULL) {
+        stage_twiddles<W>(a.tw, stw, TwBytes<W, SH::TWL>::pairs);
+        __syncthreads();
+    }
 
     auto psync = [&]() {
         if constexpr (TPP == BLOCK) __syncthreads();
         else asm volatile("bar.sync %0, %1;" ::"r"(pid + 1), "r"(TPP) : "memory");
     };
-    auto ptrs = [&](long long rho, const W *&fp, const W *&gp, W *&hp) {
-        const long long pair = a.pair0 + rho;
-        if constexpr (SRC == 1) {
-            const DevDesc<W> d = a.descs[pair];
-            fp = d.f; gp = d.g; hp = d.h;
+    auto ptrs = [&](long long rho, const W *&fp, const W *&gp, W *&hp, uint32_t &rowoff) {
+        if constexpr (FULL) {
+            const long long pair = a.pair0 + rho;
+            if constexpr (SRC == 1) {
+                const DevDesc<W> d = a.descs[pair];
+                fp = d.f; gp = d.g; hp = d.h;
+            } else {
+                fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
+            }
+            rowoff = 0;
         } else {
-            fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
+            const long long pw = rho >> (L - LROW);
+            const uint32_t row = (uint32_t)rho & ((1u << (L - LROW)) - 1u);
+            const size_t off = (size_t)pw * N + ((size_t)row << LROW);
+            fp = a.f + off; gp = a.g + off; hp = a.h + off;
+            rowoff = row << LROW;
         }
     };
     const long long stride = (long long)gridDim.x * PPC;
     for (long long rho = (long long)blockIdx.x * PPC + pid; rho < a.nrows; rho += stride) {
         const W *fp, *gp;
         W *hp;
-        ptrs(rho, fp, gp, hp);
+        uint32_t rowoff;
+        ptrs(rho, fp, gp, hp, rowoff);
         if (ptau == 0 && rho + stride < a.nrows) {
             const W *fn, *gn;
             W *hn;
-            ptrs(rho + stride, fn, gn, hn);
-            prefetch_l2(fn, N * (uint32_t)sizeof(W));
-            prefetch_l2(gn, N * (uint32_t)sizeof(W));
+            uint32_t ro;
+            ptrs(rho + stride, fn, gn, hn, ro);
+            prefetch_l2(fn, (1u << LROW) * (uint32_t)sizeof(W));
+            prefetch_l2(gn, (1u << LROW) * (uint32_t)sizeof(W));
         }
         // forward, column phase: columns c = ptau + j TPP, elements x = c + k 2^RW
         W v[2][R];
@@ -356,9 +360,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
                 v[0][j * RC + k] = fp[x];
                 v[1][j * RC + k] = gp[x];
             }
-        colf_all<W, LC, 0, CPT, TW_SMEM, R>(v[0], stw, a.c);
-        colf_all<W, LC, 0, CPT, TW_SMEM, R>(v[1], stw, a.c);
-        psync();                                            // slices free (previous pair)
+        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[0], rowoff >> RW, ftw, a.c);
+        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[1], rowoff >> RW, ftw, a.c);
+        psync();                                            // slices free (previous row)
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
 #pragma unroll
@@ -368,35 +372,40 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
                 P[(size_t)k * 2 * GR::ROWP + GR::ROWP + GR::pad(y)] = v[1][j * RC + k];
             }
         psync();
-        // forward, row phase (warp wr owns row wr)
+        // forward, row phase (warp wr owns row wr of this row group)
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const uint32_t y = b0 + ((uint32_t)k << lo0);
             v[0][k] = Srow[GR::pad(y)];
             v[1][k] = Srow[GR::ROWP + GR::pad(y)];
         }
-        fwd_all<W, L, RW, 0, 2, TW_SMEM>(v, (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
+        fwd_all<W, L, RW, 0, 2, FTW>(v, rowoff + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[0][k], v[1][k], a.c);
-        // inverse, row phase
-        dit_all<W, RW, last, TW_SMEM>(v[0], (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
+        // inverse, row phase: decimation in time for whole sequences; for a
+        // row of the split path the transposed tree, whose twiddles (like the
+        // forward ones) are contiguous runs of the plan's table
+        if constexpr (FULL) dit_all<W, RW, last, TW_SMEM>(v[0], (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
+        else inv_all<W, L, RW, last, TW_GLOBAL>(v[0], rowoff + ((uint32_t)wr << RW), lane, Srow, 0, a.tw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) Srow[GR::pad(b0 + ((uint32_t)k << lo0))] = v[0][k];
         psync();
-        // inverse, column phase, and the output at <-x>_N
+        // inverse, column phase
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
             const uint32_t col = ptau + (uint32_t)j * TPP;
 #pragma unroll
             for (int k = 0; k < RC; ++k) v[0][j * RC + k] = P[(size_t)k * 2 * GR::ROWP + GR::pad(col)];
         }
-        cold_all<W, LC, RW, 0, CPT, TPP, TW_SMEM, R>(v[0], ptau, stw, a.c);
+        if constexpr (FULL) cold_all<W, LC, RW, 0, CPT, TPP, TW_SMEM, R>(v[0], ptau, stw, a.c);
+        else colg_all<W, LC, 0, CPT, L - LROW, TW_GLOBAL, R>(v[0], rowoff >> RW, a.tw, a.c);
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
-                hp[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
+                if constexpr (FULL) hp[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
+                else hp[x] = v[0][j * RC + k];
             }
     }
 }
@@ -518,32 +527,6 @@ __device__ __forceinline__ void col_fwd_levels(W (&v)[1 << (L - LR)], const W *_
     }
 }
 
-template <typename W, int L, int LR, int J>
-__device__ __forceinline__ void col_inv_levels(W (&v)[1 << (L - LR)], const W *__restrict__ tw, const ModC<W> &c)
-{
-    constexpr int RC = 1 << (L - LR);
-    if constexpr (J < L - LR) {
-        constexpr int dg = L - LR - 1 - J;
-        if constexpr (dg == 0) {
-#pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                if (k & (1 << J)) continue;
-                gs_bfly_one<W>(v[k], v[k | (1 << J)], c);
-            }
-        } else {
-            constexpr int CNT = RC >> (J + 1);
-            W z[CNT], zp[CNT];
-            load_tw_run<W, CNT>(tw, z, zp);
-#pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                if (k & (1 << J)) continue;
-                gs_bfly<W>(v[k], v[k | (1 << J)], z[k >> (J + 1)], zp[k >> (J + 1)], c);
-            }
-        }
-        col_inv_levels<W, L, LR, J + 1>(v, tw, c);
-    }
-}
-
 template <typename W, int L, int LR, int NS, int SRC>
 __global__ void __launch_bounds__(256) k_cols_fwd(ColArgs<W> a)
 {
@@ -572,12 +555,14 @@ __global__ void __launch_bounds__(256) k_cols_fwd(ColArgs<W> a)
     }
 }
 
-// Transposed top levels of the split path, then the output stage: index
-// <-x>_N, canonical residue.  DST 0: contiguous out; 1: descriptor h.
+// Transposed top levels of the split path on column c (elements
+// x = c + k 2^LR): node twiddles k >> (J + 1), the same for every column.
+// Inputs < 2m; then the output stage: index <-x>_N, canonical residue.
+// DST 0: contiguous out; 1: descriptor h.
 template <typename W, int L, int LR, int DST>
 __global__ void __launch_bounds__(256) k_cols_inv(ColArgs<W> a)
 {
-    constexpr int RC = 1 << (L - LR);
+    constexpr int LC = L - LR, RC = 1 << LC;
     constexpr uint32_t N = 1u << L;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= a.npairs << LR) return;
@@ -590,7 +575,7 @@ __global__ void __launch_bounds__(256) k_cols_inv(ColArgs<W> a)
     W v[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
-    col_inv_levels<W, L, LR, 0>(v, a.tw, a.c);
+    colg_levels<W, LC, 0, 0, 0, TW_GLOBAL, RC>(v, 0u, a.tw, a.c);
 #pragma unroll
     for (int k = 0; k < RC; ++k) {
         const uint32_t x = col + ((uint32_t)k << LR);

@@ -91,3 +91,62 @@ def exponential_gaps(count: int, rate_per_s: float, seed: int, stream: int = 9) 
     u53 = uniform_mod(1 << 53, count, seed, stream, dtype=np.uint64).astype(np.float64)
     u = (u53 + 1.0) / float(1 << 53)
     return -np.log(u) / rate_per_s
+
+
+# ---- the same generator in torch (device-side generation of large inputs) ----
+
+def _torch_consts():
+    import torch
+
+    def s64(v):  # uint64 constant as the int64 with the same bits
+        return torch.tensor(v - (1 << 64) if v >= (1 << 63) else v, dtype=torch.int64)
+    return s64
+
+
+def _lsr(t, s):
+    """Logical right shift of int64 bit patterns."""
+    import torch
+    return (t >> s) & ((1 << (64 - s)) - 1)
+
+
+def mix64_torch(z):
+    """SplitMix64 finaliser on int64 tensors holding uint64 bit patterns."""
+    s64 = _torch_consts()
+    c1, c2 = s64(0xBF58476D1CE4E5B9).to(z.device), s64(0x94D049BB133111EB).to(z.device)
+    z = z ^ _lsr(z, 30)
+    z = z * c1
+    z = z ^ _lsr(z, 27)
+    z = z * c2
+    return z ^ _lsr(z, 31)
+
+
+def uniform_mod_torch(m: int, count: int, seed: int, stream: int, start: int = 0, device="cuda",
+                      dtype=None, chunk: int = 1 << 26):
+    """``uniform_mod`` computed with torch on ``device``: identical values."""
+    import torch
+    s64 = _torch_consts()
+    bits = max(1, int(m - 1).bit_length())
+    mask = (1 << bits) - 1
+    key = int(_key(seed, stream))
+    key_t = s64(key).to(device)
+    g_t = s64(int(G)).to(device)
+    out_dtype = dtype or (torch.int32 if m <= (1 << 31) else torch.int64)
+    out = torch.empty(count, dtype=out_dtype, device=device)
+    for c0 in range(0, count, chunk):
+        n = min(chunk, count - c0)
+        idx = torch.arange(start + c0, start + c0 + n, dtype=torch.int64, device=device)
+        vals = torch.empty(n, dtype=torch.int64, device=device)
+        todo = torch.arange(n, device=device)
+        attempt = 0
+        while todo.numel():
+            if attempt >= 64:
+                raise RuntimeError("rejection sampling did not terminate")
+            ctr = key_t + (idx[todo] * 64 + attempt) * g_t
+            v = mix64_torch(ctr)
+            v = v & mask if bits < 64 else v
+            ok = (v >= 0) & (v < m) if bits < 64 else v.to(torch.float64) < float(m)
+            vals[todo[ok]] = v[ok]
+            todo = todo[~ok]
+            attempt += 1
+        out[c0:c0 + n] = vals.to(out_dtype)
+    return out

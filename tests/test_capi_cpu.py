@@ -67,3 +67,16 @@ def test_null_arguments(ntt):
     assert lib.ntt_forward(None, None, None, 1, None) == 8
     assert lib.conv_circular(None, None, None, None, 1, None) == 8
     assert lib.conv_batched(13631489, None, 0, None) == 8
+
+
+def test_torch_generator_matches_numpy():
+    """The device-side generator used by the benchmark gives the same values
+    as the host generator used by the oracle tests."""
+    import numpy as np
+    import torch
+
+    from paper_1005_1497_gb300 import inputs
+    for m in (13631489, 641, 70525124609):
+        a = inputs.uniform_mod(m, 5000, seed=11, stream=3, start=777, dtype=np.uint64)
+        b = inputs.uniform_mod_torch(m, 5000, seed=11, stream=3, start=777, device="cpu", dtype=torch.int64)
+        assert np.array_equal(a, b.numpy().astype(np.uint64))
