@@ -35,6 +35,8 @@ WORKLOADS = {
     "conv2": (4096, 14, "uniform batch: 4096 pairs x N=2^14, m=13631489, uint32"),
     "conv1": (1, 10, "single convolution: 1 pair x N=2^10, m=13631489, uint32"),
     "conv3": (64, 19, "large transforms: 64 pairs x N=2^19, m=13631489, uint32, split column/row path"),
+    "serve5": (None, None, "serving: Poisson arrivals at 20000 req/s of convolutions with N = 2^k, k uniform on "
+                           "{8..18}, m=70525124609 (factor of F_19), uint64, continuous batching, pool-admitted"),
     "conv4": (10000, None, "uneven batch: 10000 pairs, N = 2^k with k uniform on {6..19}, m=13631489, uint32, "
                            "one batch plan replayed as a CUDA graph"),
 }
@@ -224,6 +226,8 @@ def run_ours(args):
     world, rank, local = dist_setup()
     if args.workload == "conv4":
         return run_uneven(args, world, rank, local)
+    if args.workload == "serve5":
+        return run_serve(args, world, rank, local)
     batch, L, desc = WORKLOADS[args.workload]
     N = 1 << L
     plan = ntt.Plan(M, N)
@@ -389,6 +393,66 @@ def run_uneven(args, world, rank, local):
            "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / (ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
                             "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                             "peak_src": f"{peak_src} copy bandwidth"},
+           "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_serve(args, world, rank, local):
+    """Open-loop Poisson load on the convolution server: requests are
+    submitted at their arrival times from pinned host buffers; latency is
+    submit -> result back in host memory (p50/p99 from the server)."""
+    import numpy as np
+    import torch
+
+    from paper_1005_1497_gb300 import inputs, ntt
+
+    m, rate, duration = 70525124609, 20000.0, max(0.5, min(args.steps / 1000.0, 3.0))
+    count = int(rate * duration)
+    seed = 2000 + rank
+    K = 512                                           # distinct request buffers, reused cyclically
+    lens = inputs.log_uniform_lengths(K, 8, 18, seed=seed)
+    total = int(lens.sum())
+    fbuf = inputs.uniform_mod_torch(m, total, seed, 0, device="cuda", dtype=torch.int64).cpu().pin_memory()
+    gbuf = inputs.uniform_mod_torch(m, total, seed, 1, device="cuda", dtype=torch.int64).cpu().pin_memory()
+    hbuf = torch.empty_like(fbuf).pin_memory()
+    offs = [int(v) for v in np.concatenate([[0], np.cumsum(lens)[:-1]])]
+    lens = [int(v) for v in lens]
+    fp, gp, hp = fbuf.data_ptr(), gbuf.data_ptr(), hbuf.data_ptr()
+    gaps = inputs.exponential_gaps(count, rate, seed=seed)
+    arrivals = np.cumsum(gaps)
+    srv = ntt.Server(m, pool_bytes=2 << 30, streams=4, max_batch=256, max_log2N=18)
+    # warm-up: each length once
+    for i in range(min(K, 64)):
+        st, rid = srv.submit_raw(fp + 8 * offs[i], gp + 8 * offs[i], hp + 8 * offs[i], int(lens[i]))
+        srv.wait(rid)
+    srv.reset_stats()
+    ids = [0] * count
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(count):
+            target = t0 + arrivals[i]
+            while time.perf_counter() < target:
+                pass
+            s = i % K
+            if i >= K:
+                srv.wait(ids[i - K])                  # buffer reuse: the earlier request is long done
+            st, ids[i] = srv.submit_raw(fp + 8 * offs[s], gp + 8 * offs[s], hp + 8 * offs[s], int(lens[s]))
+        srv.drain()
+        elapsed = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    mean_n = float(np.mean(lens))
+    out = {"metric": METRIC, "value": round(stats["completed"] / elapsed, 1), "unit": "req/s", "n_gpus": world,
+           "steps": count, "warmup": min(K, 64), "ms_per_step": round(elapsed * 1000.0 / count, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic (seeded counter-based; Poisson arrivals)",
+           "config": {"workload": WORKLOADS["serve5"][2], "offered_req_per_s": rate, "requests": count,
+                      "mean_N": round(mean_n, 1), "pool_bytes": 2 << 30, "streams": 4, "max_batch": 256},
+           "latency_us": {"p50": round(stats["p50_us"], 1), "p99": round(stats["p99_us"], 1),
+                          "mean": round(stats["mean_us"], 1), "max": round(stats["max_us"], 1)},
+           "server": {k: stats[k] for k in ("completed", "rejected", "batches", "max_inflight_batches",
+                                              "peak_pool_bytes")},
            "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -186,6 +186,62 @@ ntt_status ntt_batch_exec_graph(ntt_batch_t batch, ntt_stream_t stream);
 
 void ntt_batch_destroy(ntt_batch_t batch);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A convolution server: a background thread that admits requests of
+ * different power-of-two lengths against a fixed device-memory pool and
+ * batches them continuously.  A new batch (requests grouped by length, one
+ * fused launch per length) leaves on a free stream slot as soon as pool
+ * memory allows, while earlier batches are still on the GPU, so their copies
+ * and kernels overlap.  Plans and twiddle tables of every length up to
+ * 2^max_log2N stay resident.  Each request needs 3 N words of pool memory
+ * (f, g, h) from admission until its result is back in host memory.  The
+ * paper defines only the convolution; the server is the library's own. */
+typedef struct ntt_server_s *ntt_server_t;
+
+typedef struct {
+    uint64_t pool_bytes;    /* device memory for in-flight requests */
+    uint32_t streams;       /* batches in flight at once (stream slots) */
+    uint32_t max_batch;     /* requests per batch at most */
+    uint32_t max_log2N;     /* longest admissible length 2^max_log2N */
+    uint32_t reserved;
+} ntt_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches;
+    uint64_t pool_bytes, peak_pool_bytes;
+    uint32_t max_inflight_batches, reserved;
+    double p50_us, p99_us, mean_us, max_us;   /* submit -> result in host memory */
+} ntt_server_stats;
+
+/* Create a server for modulus m on the current device (allocates the pool,
+ * per-slot streams, descriptor buffers and split-path scratch; builds the
+ * plans).  Errors: as ntt_plan, NTT_ERR_ARG, NTT_ERR_OOM. */
+ntt_status ntt_server_create(uint64_t m, const ntt_server_config *cfg, ntt_server_t *out);
+
+/* Queue h = f (*) g of length N (Eq. 1).  f, g, h are HOST pointers of N
+ * words each (page-locked memory gives asynchronous copies) that must stay
+ * valid until ntt_server_wait returns for *id.  Thread-safe; returns at once.
+ * Errors: NTT_ERR_ARG, NTT_ERR_LENGTH (N above 2^max_log2N),
+ * NTT_ERR_ADMISSION (3 N words exceed the whole pool; *id is still set). */
+ntt_status ntt_server_submit(ntt_server_t srv, const void *f_host, const void *g_host, void *h_host,
+                             uint32_t N, uint64_t *id);
+
+/* Block until request id has completed (its result is in h_host) or
+ * timeout_ms elapses; then forget the request.  Returns the request's status,
+ * or NTT_ERR_TIMEOUT (the request stays queryable). */
+ntt_status ntt_server_wait(ntt_server_t srv, uint64_t id, uint32_t timeout_ms);
+
+/* Block until no request is queued or on the GPU.  NTT_ERR_TIMEOUT on expiry. */
+ntt_status ntt_server_drain(ntt_server_t srv, uint32_t timeout_ms);
+
+/* Counters and latency percentiles since creation or the last reset. */
+ntt_status ntt_server_get_stats(ntt_server_t srv, ntt_server_stats *out);
+ntt_status ntt_server_reset_stats(ntt_server_t srv);
+
+/* Stop the worker after all queued requests finish, and free the server. */
+void ntt_server_destroy(ntt_server_t srv);
+
 /* --------------------------------------------------- no-allocation variant */
 
 /* Size in bytes of the library's static split-path scratch (per GPU). */

@@ -1,0 +1,389 @@
+// ntt_serve.cu -- request loop for convolution serving: requests of
+// different power-of-two lengths arrive from host threads, are admitted
+// against a fixed device-memory pool, batched continuously (a new batch
+// leaves as soon as a stream slot and pool memory are free, while earlier
+// batches still run), convolved by the fused kernels through the resident
+// plans of the library, and copied back; per-request latency is recorded.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ntt_gb300.h"
+#include "ntt_internal.h"
+
+namespace {
+
+double now_us()
+{
+    using namespace std::chrono;
+    return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over one device region, with coalescing of free blocks.
+class Pool {
+  public:
+    void init(size_t bytes) { free_.clear(); free_[0] = bytes; size_ = bytes; used_ = peak_ = 0; }
+    static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        bytes = round(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = round(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t peak() const { return peak_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0, used_ = 0, peak_ = 0;
+};
+
+struct Req {
+    uint64_t id = 0;
+    const void *f = nullptr, *g = nullptr;
+    void *h = nullptr;
+    uint32_t N = 0;
+    int L = 0;
+    double t_submit = 0, t_done = 0;
+    ntt_status status = NTT_OK;
+    bool done = false;
+    size_t off = 0, bytes = 0;          // pool block holding f, g, h on the device
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<Req *> reqs;
+    void *descs_dev = nullptr;          // device descriptor list of this slot
+    void *descs_host = nullptr;         // pinned staging for it
+    void *scratch = nullptr;            // split-path scratch of this slot (split_words words)
+    bool busy = false;
+};
+
+}  // namespace
+
+struct ntt_server_s {
+    uint64_t m = 0;
+    int word = 64;
+    ntt_server_config cfg{};
+    void *pool_mem = nullptr;
+    Pool pool;
+    std::vector<Slot> slots;
+    std::map<int, ntt_plan_t> plans;    // log2 N -> cached plan (library-owned)
+    size_t split_words = 0;             // scratch words per slot for the split path
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> pending;
+    std::unordered_map<uint64_t, Req *> live;
+    std::vector<double> lat_us;
+    uint64_t next_id = 1, submitted = 0, completed = 0, rejected = 0, batches = 0;
+    uint32_t inflight = 0, max_inflight = 0;
+    bool stop = false;
+    ntt_status fatal = NTT_OK;
+    std::thread worker;
+    int device = 0;
+};
+
+static ntt_status server_launch(ntt_server_t s, Slot &slot, std::vector<Req *> &batch)
+{
+    const size_t elt = s->word / 8;
+    cudaStream_t st = slot.stream;
+    unsigned char *base = (unsigned char *)s->pool_mem;
+    // group by length: descriptors laid out class by class
+    std::stable_sort(batch.begin(), batch.end(), [](const Req *a, const Req *b) { return a->L > b->L; });
+    void **host = (void **)slot.descs_host;
+    for (size_t i = 0; i < batch.size(); ++i) {
+        Req *r = batch[i];
+        unsigned char *d = base + r->off;
+        const size_t seq = (size_t)r->N * elt;
+        host[3 * i + 0] = d;
+        host[3 * i + 1] = d + seq;
+        host[3 * i + 2] = d + 2 * seq;
+        if (cudaMemcpyAsync(d, r->f, seq, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d + seq, r->g, seq, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return ntt_fail(NTT_ERR_CUDA, "server: input copy");
+    }
+    if (cudaMemcpyAsync(slot.descs_dev, slot.descs_host, batch.size() * 3 * sizeof(void *), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return ntt_fail(NTT_ERR_CUDA, "server: descriptor copy");
+    for (size_t i = 0; i < batch.size();) {
+        size_t j = i;
+        while (j < batch.size() && batch[j]->L == batch[i]->L) ++j;
+        ntt_plan_t p = s->plans[batch[i]->L];
+        // pairs per scratch wave for this length (2 N words each)
+        const uint32_t wave = (uint32_t)std::max<size_t>(1, s->split_words / ((size_t)2 << batch[i]->L));
+        ntt_status e = ntt_conv_descs(p, (unsigned char *)slot.descs_dev + i * 3 * sizeof(void *), (long long)(j - i),
+                                      slot.scratch, wave, st);
+        if (e != NTT_OK) return e;
+        i = j;
+    }
+    for (Req *r : batch) {
+        const size_t seq = (size_t)r->N * elt;
+        if (cudaMemcpyAsync(r->h, base + r->off + 2 * seq, seq, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return ntt_fail(NTT_ERR_CUDA, "server: output copy");
+    }
+    if (cudaEventRecord(slot.done, st) != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "server: event");
+    slot.reqs = batch;
+    slot.busy = true;
+    return NTT_OK;
+}
+
+static void server_loop(ntt_server_t s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    const size_t elt = s->word / 8;
+    while (true) {
+        // completions
+        bool progressed = false;
+        for (Slot &slot : s->slots) {
+            if (!slot.busy) continue;
+            cudaError_t q = cudaEventQuery(slot.done);
+            if (q == cudaErrorNotReady) continue;
+            const double t = now_us();
+            for (Req *r : slot.reqs) {
+                r->status = q == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+                r->t_done = t;
+                r->done = true;
+                s->pool.release(r->off, r->bytes);
+                s->lat_us.push_back(t - r->t_submit);
+                ++s->completed;
+            }
+            slot.reqs.clear();
+            slot.busy = false;
+            --s->inflight;
+            progressed = true;
+        }
+        if (progressed) s->cv_done.notify_all();
+        if (s->stop && s->pending.empty() && s->inflight == 0) break;
+        // admission and launch: one batch per free slot
+        for (Slot &slot : s->slots) {
+            if (slot.busy || s->pending.empty()) continue;
+            std::vector<Req *> batch;
+            while (!s->pending.empty() && batch.size() < s->cfg.max_batch) {
+                Req *r = s->pending.front();
+                const size_t need = 3 * (size_t)r->N * elt;
+                size_t off;
+                if (!s->pool.alloc(need, &off)) break;    // wait for memory to free up
+                r->off = off;
+                r->bytes = need;
+                batch.push_back(r);
+                s->pending.pop_front();
+            }
+            if (batch.empty()) break;
+            ntt_status e = server_launch(s, slot, batch);
+            if (e != NTT_OK) {
+                for (Req *r : batch) {
+                    r->status = e;
+                    r->done = true;
+                    s->pool.release(r->off, r->bytes);
+                }
+                s->fatal = e;
+                s->cv_done.notify_all();
+                continue;
+            }
+            ++s->batches;
+            ++s->inflight;
+            s->max_inflight = std::max(s->max_inflight, s->inflight);
+        }
+        // sleep briefly while work is on the GPU; block when idle
+        if (s->inflight > 0) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        } else if (s->pending.empty() && !s->stop) {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        }
+    }
+}
+
+extern "C" void ntt_server_destroy(ntt_server_t s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (Slot &slot : s->slots) {
+        if (slot.stream) cudaStreamDestroy(slot.stream);
+        if (slot.done) cudaEventDestroy(slot.done);
+        cudaFree(slot.descs_dev);
+        cudaFreeHost(slot.descs_host);
+        cudaFree(slot.scratch);
+    }
+    cudaFree(s->pool_mem);
+    for (auto &kv : s->live) delete kv.second;
+    delete s;
+}
+
+extern "C" ntt_status ntt_server_create(uint64_t m, const ntt_server_config *cfg, ntt_server_t *out)
+{
+    if (!out || !cfg || cfg->pool_bytes == 0 || cfg->streams == 0 || cfg->max_batch == 0 || cfg->max_log2N == 0)
+        return ntt_fail(NTT_ERR_ARG, "ntt_server_create: invalid argument");
+    *out = nullptr;
+    ntt_server_s *s = new ntt_server_s();
+    s->m = m;
+    s->cfg = *cfg;
+    cudaGetDevice(&s->device);
+    auto bail = [&](ntt_status e) { ntt_server_destroy(s); return e; };
+    // resident plans for every admissible length (twiddle tables stay on the device)
+    size_t split_words = 0;
+    for (uint32_t L = 0; L <= cfg->max_log2N; ++L) {
+        ntt_plan_t p;
+        ntt_status e = ntt_cached_plan(m, 1u << L, &p);
+        if (e != NTT_OK) return bail(e);
+        s->plans[(int)L] = p;
+        ntt_plan_info_t info;
+        ntt_plan_get_info(p, &info);
+        s->word = (int)info.word_bits;
+        if (info.four_step) {
+            const uint32_t w = std::min<uint32_t>(info.wave, cfg->max_batch);
+            split_words = std::max(split_words, (size_t)2 * w * ((size_t)1 << L));
+        }
+    }
+    s->split_words = split_words;
+    if (cudaMalloc(&s->pool_mem, cfg->pool_bytes) != cudaSuccess) return bail(ntt_fail(NTT_ERR_OOM, "server: pool"));
+    s->pool.init(cfg->pool_bytes);
+    s->slots.resize(cfg->streams);
+    for (Slot &slot : s->slots) {
+        if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&slot.descs_dev, (size_t)cfg->max_batch * 3 * sizeof(void *)) != cudaSuccess ||
+            cudaHostAlloc(&slot.descs_host, (size_t)cfg->max_batch * 3 * sizeof(void *), cudaHostAllocDefault) != cudaSuccess)
+            return bail(ntt_fail(NTT_ERR_OOM, "server: slot resources"));
+        if (split_words) {
+            if (cudaMalloc(&slot.scratch, split_words * (s->word / 8)) != cudaSuccess)
+                return bail(ntt_fail(NTT_ERR_OOM, "server: split scratch"));
+        }
+    }
+    s->worker = std::thread(server_loop, s);
+    *out = s;
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_server_submit(ntt_server_t s, const void *f, const void *g, void *h, uint32_t N, uint64_t *id)
+{
+    if (!s || !f || !g || !h || N == 0 || (N & (N - 1)) != 0) return ntt_fail(NTT_ERR_ARG, "ntt_server_submit: invalid argument");
+    const int L = __builtin_ctz(N);
+    if ((uint32_t)L > s->cfg.max_log2N) return ntt_fail(NTT_ERR_LENGTH, "ntt_server_submit: N above the server's maximum");
+    const size_t need = Pool::round(3 * (size_t)N * (s->word / 8));
+    Req *r = new Req();
+    r->f = f; r->g = g; r->h = h; r->N = N; r->L = L;
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    if (id) *id = r->id;
+    r->t_submit = now_us();
+    ++s->submitted;
+    s->live[r->id] = r;
+    if (need > s->pool.size()) {                  // can never be admitted
+        r->status = NTT_ERR_ADMISSION;
+        r->done = true;
+        ++s->rejected;
+        return ntt_fail(NTT_ERR_ADMISSION, "ntt_server_submit: request needs %zu bytes, pool holds %zu", need, s->pool.size());
+    }
+    s->pending.push_back(r);
+    s->cv_work.notify_one();
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_server_wait(ntt_server_t s, uint64_t id, uint32_t timeout_ms)
+{
+    if (!s) return ntt_fail(NTT_ERR_ARG, "ntt_server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->live.find(id);
+    if (it == s->live.end()) return ntt_fail(NTT_ERR_ARG, "ntt_server_wait: unknown or already collected request");
+    Req *r = it->second;
+    if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; }))
+        return ntt_fail(NTT_ERR_TIMEOUT, "ntt_server_wait: request %llu not done in %u ms", (unsigned long long)id, timeout_ms);
+    const ntt_status st = r->status;
+    s->live.erase(it);
+    delete r;
+    return st;
+}
+
+extern "C" ntt_status ntt_server_drain(ntt_server_t s, uint32_t timeout_ms)
+{
+    if (!s) return ntt_fail(NTT_ERR_ARG, "ntt_server_drain: NULL server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        return s->pending.empty() && s->inflight == 0;
+    });
+    if (!ok) return ntt_fail(NTT_ERR_TIMEOUT, "ntt_server_drain: work still pending after %u ms", timeout_ms);
+    return s->fatal;
+}
+
+extern "C" ntt_status ntt_server_get_stats(ntt_server_t s, ntt_server_stats *out)
+{
+    if (!s || !out) return ntt_fail(NTT_ERR_ARG, "ntt_server_get_stats: invalid argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof *out);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->batches = s->batches;
+    out->max_inflight_batches = s->max_inflight;
+    out->pool_bytes = s->pool.size();
+    out->peak_pool_bytes = s->pool.peak();
+    if (!s->lat_us.empty()) {
+        std::vector<double> v = s->lat_us;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double p) { return v[std::min(v.size() - 1, (size_t)(p * (double)(v.size() - 1) + 0.5))]; };
+        out->p50_us = pct(0.50);
+        out->p99_us = pct(0.99);
+        out->max_us = v.back();
+        double sum = 0;
+        for (double x : v) sum += x;
+        out->mean_us = sum / (double)v.size();
+    }
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_server_reset_stats(ntt_server_t s)
+{
+    if (!s) return ntt_fail(NTT_ERR_ARG, "ntt_server_reset_stats: NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat_us.clear();
+    s->submitted = s->completed = s->rejected = s->batches = 0;
+    s->max_inflight = 0;
+    return NTT_OK;
+}

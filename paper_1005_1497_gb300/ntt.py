@@ -42,6 +42,13 @@ SIGNATURES = {
     "ntt_batch_exec_graph": (_INT, [_VP, _VP]),
     "ntt_batch_destroy": (None, [_VP]),
     "ntt_check_range": (_INT, [_VP, _VP, _SZ, ctypes.POINTER(_U64), _VP]),
+    "ntt_server_create": (_INT, [_U64, _VP, ctypes.POINTER(_VP)]),
+    "ntt_server_submit": (_INT, [_VP, _VP, _VP, _VP, _U32, ctypes.POINTER(_U64)]),
+    "ntt_server_wait": (_INT, [_VP, _U64, _U32]),
+    "ntt_server_drain": (_INT, [_VP, _U32]),
+    "ntt_server_get_stats": (_INT, [_VP, _VP]),
+    "ntt_server_reset_stats": (_INT, [_VP]),
+    "ntt_server_destroy": (None, [_VP]),
 }
 
 
@@ -267,3 +274,67 @@ def ntt_check_range(plan: Plan, x: torch.Tensor, stream=None) -> int:
     if st not in (NTT_OK, 4):
         _check(st, "ntt_check_range")
     return int(bad.value)
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_uint64), ("streams", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("max_log2N", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("pool_bytes", ctypes.c_uint64), ("peak_pool_bytes", ctypes.c_uint64),
+                ("max_inflight_batches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double)]
+
+
+class Server:
+    """``ntt_server_create``: continuous-batching convolution server (host buffers)."""
+
+    def __init__(self, m: int, pool_bytes: int = 1 << 30, streams: int = 4, max_batch: int = 256, max_log2N: int = 18):
+        cfg = ServerConfig(pool_bytes, streams, max_batch, max_log2N, 0)
+        h = ctypes.c_void_p()
+        _check(lib().ntt_server_create(m, ctypes.byref(cfg), ctypes.byref(h)), "ntt_server_create")
+        self.handle = h
+        self.m = m
+
+    def submit(self, f: torch.Tensor, g: torch.Tensor, h: torch.Tensor) -> int:
+        """Queue h = f (*) g; CPU tensors (pinned for asynchronous copies) that
+        must stay alive until wait() returns.  Returns the request id."""
+        rid = ctypes.c_uint64(0)
+        st = lib().ntt_server_submit(self.handle, f.data_ptr(), g.data_ptr(), h.data_ptr(), f.numel(),
+                                     ctypes.byref(rid))
+        if st != NTT_OK:
+            raise NttError(st, "ntt_server_submit", lib().ntt_last_error().decode(errors="replace"))
+        return rid.value
+
+    def submit_raw(self, f_ptr: int, g_ptr: int, h_ptr: int, N: int) -> tuple[int, int]:
+        rid = ctypes.c_uint64(0)
+        st = lib().ntt_server_submit(self.handle, f_ptr, g_ptr, h_ptr, N, ctypes.byref(rid))
+        return st, rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 60000):
+        _check(lib().ntt_server_wait(self.handle, rid, timeout_ms), "ntt_server_wait")
+
+    def drain(self, timeout_ms: int = 600000):
+        _check(lib().ntt_server_drain(self.handle, timeout_ms), "ntt_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ntt_server_get_stats(self.handle, ctypes.byref(st)), "ntt_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_ if k != "reserved"}
+
+    def reset_stats(self):
+        _check(lib().ntt_server_reset_stats(self.handle), "ntt_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().ntt_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
