@@ -101,6 +101,18 @@ __device__ __forceinline__ void ct_bfly_one(W &a, W &b, const ModC<W> &c)
     b = a0 - b + c.m;
 }
 
+// Butterfly with the twiddle 1 on inputs bounded by B (B a multiple of m):
+// outputs < 2B, no product.  Used where the twiddle is known to be 1 at
+// compile time (node 0 of a forward level, position 0 of an inverse level)
+// and the doubled bound still fits the word (see the bound notes below).
+template <typename W>
+__device__ __forceinline__ void ct_bfly_unit(W &a, W &b, W B)
+{
+    W a0 = a;
+    a = a0 + b;
+    b = a0 - b + B;
+}
+
 // Transposed (Gentleman-Sande) node butterfly on inputs < 2m; outputs < 2m.
 template <typename W>
 __device__ __forceinline__ void gs_bfly(W &a, W &b, W z, W zp, const ModC<W> &c)
@@ -251,7 +263,12 @@ __device__ __forceinline__ void stage_twiddles(const W *__restrict__ tw, W *stw,
 }
 
 // One forward level: element bit b = lo_P + JJ, global level L-1-b.
-template <typename W, int L, int LR, int P, int JJ, int NS, int TWS>
+// Z0: the node base of this pass is known to be 0 (first pass of a whole
+// sequence), so node 0 has the twiddle 1.  Bound note: inputs < m, level 0
+// leaves < 2m and every node-0 butterfly of levels 1..4 doubles the bound
+// (< 2^(d+1) m after level d), the others add 2m: at most 32m + 2m (L - 5)
+// after the forward, below 50m for L <= 14.
+template <typename W, int L, int LR, int P, int JJ, int NS, int TWS, bool Z0 = false>
 __device__ __forceinline__ void fwd_level(W (&v)[NS][Geo<W, LR>::R], uint32_t xbase,
                                           const W *__restrict__ tw, const ModC<W> &c)
 {
@@ -269,6 +286,7 @@ __device__ __forceinline__ void fwd_level(W (&v)[NS][Geo<W, LR>::R], uint32_t xb
     } else {
         constexpr int CNT = R >> (JJ + 1);      // distinct nodes touched by this thread
         constexpr int CH = (CNT >= 2 && tw_per_chunk<W>() == 2) ? 2 : 1;
+        constexpr bool UNIT0 = Z0 && P == 0 && dg <= 4;
         const uint32_t nb = xbase >> (b + 1);   // aligned to CNT
 #pragma unroll
         for (int t0 = 0; t0 < CNT; t0 += CH) {
@@ -280,28 +298,31 @@ __device__ __forceinline__ void fwd_level(W (&v)[NS][Geo<W, LR>::R], uint32_t xb
                 for (int j = 0; j < (1 << JJ); ++j) {
                     const int k = ((t0 + tt) << (JJ + 1)) | j;
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) ct_bfly<W>(v[s][k], v[s][k | (1 << JJ)], z[tt], zp[tt], c);
+                    for (int s = 0; s < NS; ++s) {
+                        if (UNIT0 && t0 + tt == 0) ct_bfly_unit<W>(v[s][k], v[s][k | (1 << JJ)], c.m << dg);
+                        else ct_bfly<W>(v[s][k], v[s][k | (1 << JJ)], z[tt], zp[tt], c);
+                    }
                 }
         }
     }
 }
 
 // Forward levels of pass P, highest element bit first.
-template <typename W, int L, int LR, int P, int JJ, int NS, int TWS>
+template <typename W, int L, int LR, int P, int JJ, int NS, int TWS, bool Z0>
 __device__ __forceinline__ void fwd_levels(W (&v)[NS][Geo<W, LR>::R], uint32_t xbase,
                                            const W *__restrict__ tw, const ModC<W> &c)
 {
     if constexpr (JJ >= 0) {
-        fwd_level<W, L, LR, P, JJ, NS, TWS>(v, xbase, tw, c);
-        fwd_levels<W, L, LR, P, JJ - 1, NS, TWS>(v, xbase, tw, c);
+        fwd_level<W, L, LR, P, JJ, NS, TWS, Z0>(v, xbase, tw, c);
+        fwd_levels<W, L, LR, P, JJ - 1, NS, TWS, Z0>(v, xbase, tw, c);
     }
 }
 
-template <typename W, int L, int LR, int P, int NS, int TWS>
+template <typename W, int L, int LR, int P, int NS, int TWS, bool Z0 = false>
 __device__ __forceinline__ void fwd_pass(W (&v)[NS][Geo<W, LR>::R], uint32_t xbase,
                                          const W *__restrict__ tw, const ModC<W> &c)
 {
-    fwd_levels<W, L, LR, P, Geo<W, LR>::nb(P) - 1, NS, TWS>(v, xbase, tw, c);
+    fwd_levels<W, L, LR, P, Geo<W, LR>::nb(P) - 1, NS, TWS, Z0>(v, xbase, tw, c);
 }
 
 // One transposed (inverse-direction) level.
@@ -376,7 +397,12 @@ __host__ __device__ constexpr int brv_c(int j)
     return r;
 }
 
-// Level l = lo_P + JJ of the inverse on one sequence.
+// Level l = lo_P + JJ of the inverse on one sequence.  In the first pass
+// (lo = 0) every thread's run starts at entry 0, whose twiddle is 1: those
+// butterflies skip the product.  Bound note: inputs < 2m, level 0 leaves
+// < 4m, the unit butterflies of levels 1..4 double it (< 2^(l+2) m after
+// level l), the others add 2m: at most 64m + 2m (L - 5), below 82m for
+// L <= 14, and the final Shoup reduction accepts any word.
 template <typename W, int LR, int P, int JJ, int TWS>
 __device__ __forceinline__ void dit_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
                                           const W *__restrict__ tw, const ModC<W> &c)
@@ -408,7 +434,8 @@ __device__ __forceinline__ void dit_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
 #pragma unroll
                 for (int hi = 0; hi < (R >> (JJ + 1)); ++hi) {
                     const int k = (hi << (JJ + 1)) | j;
-                    ct_bfly<W>(v[k], v[k | (1 << JJ)], z[tt], zp[tt], c);
+                    if (lo == 0 && l <= 4 && t0 + tt == 0) ct_bfly_unit<W>(v[k], v[k | (1 << JJ)], c.m << (l + 1));
+                    else ct_bfly<W>(v[k], v[k | (1 << JJ)], z[tt], zp[tt], c);
                 }
             }
         }
@@ -449,15 +476,15 @@ __device__ __forceinline__ void exchange(W (&v)[NS][Geo<W, LR>::R], W *S, uint32
 }
 
 // All forward passes P = FROM .. NPASS-1 (registers start in layout FROM).
-template <typename W, int L, int LR, int P, int NS, int TWS>
+template <typename W, int L, int LR, int P, int NS, int TWS, bool Z0 = false>
 __device__ __forceinline__ void fwd_all(W (&v)[NS][Geo<W, LR>::R], uint32_t rowoff, uint32_t tau,
                                         W *S, int gid, const W *__restrict__ tw, const ModC<W> &c)
 {
     using G = Geo<W, LR>;
-    fwd_pass<W, L, LR, P, NS, TWS>(v, rowoff + G::base(P, tau), tw, c);
+    fwd_pass<W, L, LR, P, NS, TWS, Z0>(v, rowoff + G::base(P, tau), tw, c);
     if constexpr (P + 1 < G::NPASS) {
         exchange<W, LR, P, P + 1, NS>(v, S, tau, gid);
-        fwd_all<W, L, LR, P + 1, NS, TWS>(v, rowoff, tau, S, gid, tw, c);
+        fwd_all<W, L, LR, P + 1, NS, TWS, Z0>(v, rowoff, tau, S, gid, tw, c);
     }
 }
 

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
             v[0][k] = fp[b0 + ((uint32_t)k << lo0)];
             v[1][k] = gp[b0 + ((uint32_t)k << lo0)];
         }
-        fwd_all<W, L, L, 0, 2, TW_SMEM>(v, 0u, tau, S, gid, stw, a.c);
+        fwd_all<W, L, L, 0, 2, TW_SMEM, true>(v, 0u, tau, S, gid, stw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[0][k], v[1][k], a.c);
         dit_all<W, L, last, TW_SMEM>(v[0], 0u, tau, S, gid, stw, a.c);
@@ -165,7 +165,9 @@ __device__ __forceinline__ void colf_levels(W (&v)[RR], uint32_t rowbase, const 
 #pragma unroll
                     for (int j = 0; j < (1 << J); ++j) {
                         const int k = ((t0 + tt) << (J + 1)) | j;
-                        ct_bfly<W>(v[OFF + k], v[OFF + (k | (1 << J))], z[tt], zp[tt], c);
+                        // whole sequence: node 0 has the twiddle 1 (bound note at fwd_level)
+                        if (DG0 == 0 && dg <= 4 && t0 + tt == 0) ct_bfly_unit<W>(v[OFF + k], v[OFF + (k | (1 << J))], c.m << dg);
+                        else ct_bfly<W>(v[OFF + k], v[OFF + (k | (1 << J))], z[tt], zp[tt], c);
                     }
             }
         }
@@ -336,12 +338,31 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
             rowoff = row << LROW;
         }
     };
+    // v[1] carries this row's f, loaded during the previous row's inverse
+    // phases (the registers are free after the pointwise product); g is
+    // loaded into v[0] while f's column levels run.  (Staging g in the idle
+    // g slices with cp.async instead was measured slower: the extra shared
+    // memory traffic costs more than the latency it hides.)
+    auto load_cols = [&](const W *src, W (&dst)[R]) {
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) dst[j * RC + k] = src[ptau + (uint32_t)j * TPP + ((uint32_t)k << RW)];
+    };
     const long long stride = (long long)gridDim.x * PPC;
-    for (long long rho = (long long)blockIdx.x * PPC + pid; rho < a.nrows; rho += stride) {
-        const W *fp, *gp;
-        W *hp;
-        uint32_t rowoff;
+    long long rho = (long long)blockIdx.x * PPC + pid;
+    W v[2][R];
+    const W *fp = nullptr, *gp = nullptr;
+    W *hp = nullptr;
+    uint32_t rowoff = 0;
+    if (rho < a.nrows) {
         ptrs(rho, fp, gp, hp, rowoff);
+        load_cols(fp, v[1]);
+    }
+    for (; rho < a.nrows; rho += stride) {
+        W *const hcur = hp;
+        const uint32_t rcur = rowoff;
+        const W *gcur = gp;
         if (ptau == 0 && rho + stride < a.nrows) {
             const W *fn, *gn;
             W *hn;
@@ -351,17 +372,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
             prefetch_l2(gn, (1u << LROW) * (uint32_t)sizeof(W));
         }
         // forward, column phase: columns c = ptau + j TPP, elements x = c + k 2^RW
-        W v[2][R];
-#pragma unroll
-        for (int j = 0; j < CPT; ++j)
-#pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
-                v[0][j * RC + k] = fp[x];
-                v[1][j * RC + k] = gp[x];
-            }
-        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[0], rowoff >> RW, ftw, a.c);
-        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[1], rowoff >> RW, ftw, a.c);
+        load_cols(gcur, v[0]);
+        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[1], rcur >> RW, ftw, a.c);
+        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[0], rcur >> RW, ftw, a.c);
         psync();                                            // slices free (previous row)
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
@@ -369,7 +382,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
             for (int k = 0; k < RC; ++k) {
                 const uint32_t y = ptau + (uint32_t)j * TPP;
                 P[(size_t)k * 2 * GR::ROWP + GR::pad(y)] = v[0][j * RC + k];
-                P[(size_t)k * 2 * GR::ROWP + GR::ROWP + GR::pad(y)] = v[1][j * RC + k];
+                P[(size_t)k * 2 * GR::ROWP + GR::ROWP + GR::pad(y)] = v[1][j * RC + k];   // (v[0] = g, v[1] = f)
             }
         psync();
         // forward, row phase (warp wr owns row wr of this row group)
@@ -379,14 +392,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
             v[0][k] = Srow[GR::pad(y)];
             v[1][k] = Srow[GR::ROWP + GR::pad(y)];
         }
-        fwd_all<W, L, RW, 0, 2, FTW>(v, rowoff + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
+        fwd_all<W, L, RW, 0, 2, FTW>(v, rcur + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[0][k], v[1][k], a.c);
+        for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[1][k], v[0][k], a.c);
+        if (rho + stride < a.nrows) {
+            ptrs(rho + stride, fp, gp, hp, rowoff);
+            load_cols(fp, v[1]);                            // next row's f
+        }
         // inverse, row phase: decimation in time for whole sequences; for a
         // row of the split path the transposed tree, whose twiddles (like the
         // forward ones) are contiguous runs of the plan's table
         if constexpr (FULL) dit_all<W, RW, last, TW_SMEM>(v[0], (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
-        else inv_all<W, L, RW, last, TW_GLOBAL>(v[0], rowoff + ((uint32_t)wr << RW), lane, Srow, 0, a.tw, a.c);
+        else inv_all<W, L, RW, last, TW_GLOBAL>(v[0], rcur + ((uint32_t)wr << RW), lane, Srow, 0, a.tw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) Srow[GR::pad(b0 + ((uint32_t)k << lo0))] = v[0][k];
         psync();
@@ -398,14 +415,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
             for (int k = 0; k < RC; ++k) v[0][j * RC + k] = P[(size_t)k * 2 * GR::ROWP + GR::pad(col)];
         }
         if constexpr (FULL) cold_all<W, LC, RW, 0, CPT, TPP, TW_SMEM, R>(v[0], ptau, stw, a.c);
-        else colg_all<W, LC, 0, CPT, L - LROW, TW_GLOBAL, R>(v[0], rowoff >> RW, a.tw, a.c);
+        else colg_all<W, LC, 0, CPT, L - LROW, TW_GLOBAL, R>(v[0], rcur >> RW, a.tw, a.c);
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
-                if constexpr (FULL) hp[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
-                else hp[x] = v[0][j * RC + k];
+                if constexpr (FULL) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
+                else hcur[x] = v[0][j * RC + k];
             }
     }
 }
