@@ -145,13 +145,24 @@ def barrier(world):
 
 
 def max_over_ranks(world, value: float) -> float:
+    """Largest value over all ranks (the step time of the slowest GPU)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_pairs(total: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous share [start, end) of `total` independent pairs for `rank`
+    (used when a fixed job is split across GPUs; the benchmark itself gives
+    every rank its own batch of the same size, i.e. weak scaling)."""
+    base, extra = divmod(total, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
 
 
 def traffic_from_profile(kernel_tag: str):
@@ -230,6 +241,7 @@ def run_ours(args):
         return run_serve(args, world, rank, local)
     batch, L, desc = WORKLOADS[args.workload]
     N = 1 << L
+    tuned = ntt.ntt_autotune(M, N, batch) if L > 14 else None     # split path: pick pairs per wave
     plan = ntt.Plan(M, N)
     # inputs from the shared seeded generator (computed on the device), resident in HBM
     seed = 1000 + rank
@@ -290,6 +302,9 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
     }
+    if tuned:
+        out["config"]["schedule"] = {"pairs_per_wave": tuned["wave"], "heuristic": tuned["default_wave"],
+                                     "tuned_ms": round(tuned["ms"], 4), "heuristic_ms": round(tuned["default_ms"], 4)}
 
     if not args.quick:
         # plain form: one launch per butterfly stage over the whole batch
@@ -361,6 +376,11 @@ def run_uneven(args, world, rank, local):
     g = inputs.uniform_mod_torch(M, total, seed, 1, device="cuda")
     h = torch.empty_like(f)
     triples = [(f[o:o + n], g[o:o + n], h[o:o + n]) for o, n in zip(offs.tolist(), lens.tolist())]
+    schedule = {}
+    for k in range(15, 20):                          # split-path classes: autotune pairs per wave
+        cnt = int((lens == (1 << k)).sum())
+        if cnt:
+            schedule[f"2^{k}"] = ntt.ntt_autotune(M, 1 << k, cnt)["wave"]
     bp = ntt.BatchPlan(M, triples)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -386,7 +406,8 @@ def run_uneven(args, world, rank, local):
     out = {"metric": METRIC, "value": round(count * world * 1000.0 / ms, 1), "unit": "conv/s", "n_gpus": world,
            "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded counter-based)",
-           "config": {"workload": desc, "pairs": count, "elements": total, "m": M},
+           "config": {"workload": desc, "pairs": count, "elements": total, "m": M,
+                      "schedule_pairs_per_wave": schedule},
            "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1),
                         "unit": "Gmodmul/s", "frac": round(alu_ach / alu_peak, 4), "traffic": None,
                         "kernel": "all length classes of one step (graph replay)"},

@@ -186,6 +186,28 @@ ntt_status ntt_batch_exec_graph(ntt_batch_t batch, ntt_stream_t stream);
 
 void ntt_batch_destroy(ntt_batch_t batch);
 
+/* -------------------------------------------------------------- autotuning */
+
+typedef struct {
+    uint32_t wave;          /* chosen pairs per scratch wave (split path) */
+    uint32_t default_wave;  /* the heuristic choice (4 rows per SM per wave) */
+    double ms;              /* time of one convolution call over `batch` pairs with `wave` */
+    double default_ms;      /* the same with the heuristic wave (0 if not measured) */
+} ntt_tune_result;
+
+/* Time the split path's candidate schedules (pairs per scratch wave: powers
+ * of two, the heuristic, all pairs) for `batch` pairs of length N modulo m
+ * on the current GPU, and record the fastest for (GPU name, word size,
+ * log2 N); plans created afterwards use it.  Lengths that fit one block
+ * have no schedule to choose and return the default.  Synchronous;
+ * allocates its own buffers.  Errors: as ntt_plan, NTT_ERR_OOM, NTT_ERR_CUDA. */
+ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tune_result *out);
+
+/* Write / read the recorded schedules as JSON ({"schedules": [...]}, one
+ * entry per GPU name, word size and log2 N).  Errors: NTT_ERR_ARG. */
+ntt_status ntt_autotune_save(const char *path);
+ntt_status ntt_autotune_load(const char *path);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A convolution server: a background thread that admits requests of

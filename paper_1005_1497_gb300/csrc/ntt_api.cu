@@ -187,7 +187,8 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         // Enough pairs per wave to fill every SM with rows several times over,
         // while the scratch (2 N words per pair) stays a few tens of MB.
         const uint64_t rows_per_pair = 1ull << (L - p->LR);
-        uint64_t wave = (uint64_t)p->nsm * 4 / rows_per_pair;
+        uint64_t wave = ntt_tuned_wave(word, L);       // autotuned schedule, if any
+        if (wave == 0) wave = (uint64_t)p->nsm * 4 / rows_per_pair;
         if (wave < 1) wave = 1;
         p->wave = (uint32_t)wave;
         if (cudaMalloc(&p->scratch, 2 * wave * N * elt) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: scratch");

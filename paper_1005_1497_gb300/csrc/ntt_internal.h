@@ -18,3 +18,5 @@ ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs_dev, long long count, 
 // split-path scratch (wave pairs of 2 N words); scratch unused when N fits one block.
 ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, void *h, long long batch,
                                  void *scratch, uint32_t wave, cudaStream_t st);
+// Tuned pairs per scratch wave for (word size, log2 N) on the current GPU, 0 if untuned.
+uint32_t ntt_tuned_wave(int word_bits, int log2N);

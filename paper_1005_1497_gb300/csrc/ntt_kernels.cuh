@@ -355,11 +355,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
     const W *fp = nullptr, *gp = nullptr;
     W *hp = nullptr;
     uint32_t rowoff = 0;
-    if (rho < a.nrows) {
+    // (split rows keep no prefetched registers across their inverse: it reads
+    // its twiddles from global memory and needs the registers itself)
+    constexpr bool PREF = FULL;
+    if (PREF && rho < a.nrows) {
         ptrs(rho, fp, gp, hp, rowoff);
         load_cols(fp, v[1]);
     }
     for (; rho < a.nrows; rho += stride) {
+        if (!PREF) {
+            ptrs(rho, fp, gp, hp, rowoff);
+            load_cols(fp, v[1]);
+        }
         W *const hcur = hp;
         const uint32_t rcur = rowoff;
         const W *gcur = gp;
@@ -395,7 +402,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
         fwd_all<W, L, RW, 0, 2, FTW>(v, rcur + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[1][k], v[0][k], a.c);
-        if (rho + stride < a.nrows) {
+        if (PREF && rho + stride < a.nrows) {
             ptrs(rho + stride, fp, gp, hp, rowoff);
             load_cols(fp, v[1]);                            // next row's f
         }

@@ -42,6 +42,9 @@ SIGNATURES = {
     "ntt_batch_exec_graph": (_INT, [_VP, _VP]),
     "ntt_batch_destroy": (None, [_VP]),
     "ntt_check_range": (_INT, [_VP, _VP, _SZ, ctypes.POINTER(_U64), _VP]),
+    "ntt_autotune": (_INT, [_U64, _U32, _SZ, _VP]),
+    "ntt_autotune_save": (_INT, [ctypes.c_char_p]),
+    "ntt_autotune_load": (_INT, [ctypes.c_char_p]),
     "ntt_server_create": (_INT, [_U64, _VP, ctypes.POINTER(_VP)]),
     "ntt_server_submit": (_INT, [_VP, _VP, _VP, _VP, _U32, ctypes.POINTER(_U64)]),
     "ntt_server_wait": (_INT, [_VP, _U64, _U32]),
@@ -338,3 +341,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("wave", ctypes.c_uint32), ("default_wave", ctypes.c_uint32), ("ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double)]
+
+
+def ntt_autotune(m: int, N: int, batch: int) -> dict:
+    """Pick the split path's pairs-per-wave for (m, N) and `batch` pairs on this GPU."""
+    r = TuneResult()
+    _check(lib().ntt_autotune(m, N, batch, ctypes.byref(r)), "ntt_autotune")
+    return {"wave": r.wave, "default_wave": r.default_wave, "ms": r.ms, "default_ms": r.default_ms}
+
+
+def ntt_autotune_save(path: str):
+    _check(lib().ntt_autotune_save(path.encode()), "ntt_autotune_save")
+
+
+def ntt_autotune_load(path: str):
+    _check(lib().ntt_autotune_load(path.encode()), "ntt_autotune_load")

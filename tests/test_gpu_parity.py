@@ -205,3 +205,22 @@ def test_host_buffers(ntt, orc):
         want = host(ntt.conv_circular(plan, ft.cuda(), gt.cuda()))
         assert np.array_equal(ht.numpy().astype(np.uint64), want)
         assert np.array_equal(want[:1], ref_conv(orc, f[:1], g[:1], M, plan.omega))
+
+
+def test_autotune_schedule_roundtrip(ntt, orc, tmp_path):
+    """The autotuner picks a wave for the split path, plans created afterwards
+    use it, results stay bit-exact, and the table survives save/load."""
+    N, batch = 1 << 17, 24
+    r = ntt.ntt_autotune(M, N, batch)
+    assert r["wave"] >= 1 and r["ms"] > 0
+    plan = ntt.Plan(M, N)
+    assert plan.wave == r["wave"]
+    f, g = pairs(M, 3, N, seed=4242)
+    h = host(ntt.conv_circular(plan, dev(f, 32), dev(g, 32)))
+    assert np.array_equal(h[:1], ref_conv(orc, f[:1], g[:1], M, plan.omega))
+    path = str(tmp_path / "sched.json")
+    ntt.ntt_autotune_save(path)
+    ntt.ntt_autotune_load(path)
+    assert '"log2N": 17' in open(path).read()
+    small = ntt.ntt_autotune(M, 1 << 10, 4)                 # one block per sequence: nothing to tune
+    assert small["wave"] == small["default_wave"] == 0
