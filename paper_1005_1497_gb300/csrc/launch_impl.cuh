@@ -44,6 +44,47 @@ static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t 
     }
 }
 
+template <typename W, int L>
+static size_t full_smem_of()
+{
+    constexpr int RW = Arith<W>::RB + 5;
+    if constexpr (L <= RW) return TwBytes<W, L>::v + RowShape<W, L, L>::smem(2);
+    else if constexpr (L <= LRMax<W>::v) return CRShape<W, L>::smem;
+    else return 0;
+}
+
+template <typename W>
+size_t Launch<W>::conv_full_smem(int L)
+{
+    switch (L) {
+#define S(X) case X: return full_smem_of<W, X>();
+    S(0) S(1) S(2) S(3) S(4) S(5) S(6) S(7) S(8) S(9) S(10) S(11) S(12) S(13) S(14)
+#undef S
+    default: return 0;
+    }
+}
+
+template <typename W, int HI>
+static cudaError_t launch_persistent(const PersistArgs<W> &a, int grid, size_t smem, cudaStream_t st)
+{
+    static const cudaError_t init = [] {
+        size_t most = 0;
+        for (int L = 0; L <= HI; ++L) most = std::max(most, Launch<W>::conv_full_smem(L));
+        return cudaFuncSetAttribute(k_conv_persistent<W, HI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    }();
+    if (init != cudaSuccess) return init;
+    k_conv_persistent<W, HI><<<grid, BLOCK, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t Launch<W>::conv_persistent(const PersistArgs<W> &a, int lmax, int grid, size_t smem, cudaStream_t st)
+{
+    constexpr int RW = Arith<W>::RB + 5;
+    if (lmax <= RW) return launch_persistent<W, RW>(a, grid, smem, st);
+    return launch_persistent<W, LRMax<W>::v>(a, grid, smem, st);
+}
+
 template <typename W>
 int Launch<W>::pairs_per_block(int L)
 {

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -416,4 +417,50 @@ ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, voi
         : conv_dispatch<uint64_t>(p, (const uint64_t *)f, (const uint64_t *)g, (uint64_t *)h, nullptr, 0, batch,
                                   (uint64_t *)scratch, wave, st);
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (scratch)");
+}
+
+const void *ntt_plan_twiddles(ntt_plan_t p) { return p ? p->tw : nullptr; }
+
+void ntt_plan_modc(ntt_plan_t p, void *out, size_t bytes)
+{
+    if (!p || !out) return;
+    if (p->word == 32) memcpy(out, &p->c32, std::min(bytes, sizeof p->c32));
+    else memcpy(out, &p->c64, std::min(bytes, sizeof p->c64));
+}
+
+// Longest length a batch plan folds into its persistent launch: the
+// one-warp lengths by default (their bodies share one kernel without
+// spilling); NTT_PERSIST_LMAX raises it to every whole-sequence length.
+int ntt_persist_lmax(int word_bits)
+{
+    const int rw = word_bits == 32 ? ntt::Arith<uint32_t>::RB + 5 : ntt::Arith<uint64_t>::RB + 5;
+    const int lr = word_bits == 32 ? ntt::LRMax<uint32_t>::v : ntt::LRMax<uint64_t>::v;
+    const char *e = getenv("NTT_PERSIST_LMAX");
+    int v = e ? atoi(e) : rw;
+    return v <= rw ? rw : lr;
+}
+
+size_t ntt_full_smem(int word_bits, int log2N)
+{
+    return word_bits == 32 ? Launch<uint32_t>::conv_full_smem(log2N) : Launch<uint64_t>::conv_full_smem(log2N);
+}
+
+int ntt_num_sms() { return num_sms(); }
+
+ntt_status ntt_launch_persistent(int word_bits, const void *descs, const void *items, int nitems, int *counter,
+                                 const void *cls, int lmax, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        if (word_bits == 32) {
+            ntt::PersistArgs<uint32_t> a{(const DevDesc<uint32_t> *)descs, (const ntt::WorkItem *)items, nitems, counter, {}};
+            memcpy(a.cls, cls, sizeof a.cls);
+            e = Launch<uint32_t>::conv_persistent(a, lmax, grid, smem, st);
+        } else {
+            ntt::PersistArgs<uint64_t> a{(const DevDesc<uint64_t> *)descs, (const ntt::WorkItem *)items, nitems, counter, {}};
+            memcpy(a.cls, cls, sizeof a.cls);
+            e = Launch<uint64_t>::conv_persistent(a, lmax, grid, smem, st);
+        }
+    }
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "persistent launch");
 }

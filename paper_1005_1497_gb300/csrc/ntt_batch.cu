@@ -15,6 +15,7 @@
 
 #include "../../include/ntt_gb300.h"
 #include "ntt_internal.h"
+#include "ntt_launch.h"
 
 
 
@@ -56,6 +57,14 @@ struct ntt_batch_s {
     uint64_t m = 0;
     int word = 32;
     std::vector<BatchClass> classes;
+    // whole-sequence lengths: one persistent launch over a work list
+    void *items = nullptr;           // ntt::WorkItem[nitems]
+    int nitems = 0;
+    std::vector<unsigned char> cls;  // host copy of ntt::ClassParam<W>[LR_max + 1], passed by value
+    int *counter = nullptr;
+    size_t persist_smem = 0;
+    int persist_grid = 0;
+    int persist_lmax = 0;            // longest length among the items
     void *descs = nullptr;           // DevDesc<W>[count], grouped by class
     size_t count = 0;
     std::vector<cudaStream_t> streams;
@@ -73,6 +82,8 @@ extern "C" void ntt_batch_destroy(ntt_batch_t b)
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto &c : b->classes) cudaFree(c.scratch);
     cudaFree(b->descs);
+    cudaFree(b->items);
+    cudaFree(b->counter);
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto e : b->done) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -135,11 +146,49 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
         }
     }
 
-    // longest-processing-time assignment of classes to up to 4 streams
-    const int K = (int)std::min<size_t>(4, b->classes.size());
-    std::vector<double> load(K, 0.0);
+    // Short lengths become work items of a single persistent launch on
+    // stream 0; each item covers two rounds of a block's rows in flight.
+    // Longer lengths keep their own launches, spread over streams 1..K-1 by
+    // longest-processing-time.
+    const int lrmax = b->word == 32 ? ntt::LRMax<uint32_t>::v : ntt::LRMax<uint64_t>::v;
+    const int plmax = ntt_persist_lmax(b->word);
+    std::vector<ntt::WorkItem> items;
+    std::vector<unsigned char> &cls = b->cls;
+    cls.assign((size_t)(lrmax + 1) * std::max(sizeof(ntt::ClassParam<uint32_t>), sizeof(ntt::ClassParam<uint64_t>)), 0);
+    const size_t cps = b->word == 32 ? sizeof(ntt::ClassParam<uint32_t>) : sizeof(ntt::ClassParam<uint64_t>);
+    size_t nsplit = 0;             // classes with their own launches
     for (auto &c : b->classes) {
-        int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        if (c.L > plmax) { ++nsplit; continue; }
+        b->persist_lmax = std::max(b->persist_lmax, c.L);
+        c.stream = -1;                                   // runs inside the persistent launch
+        const int ppb = b->word == 32 ? ntt::Launch<uint32_t>::pairs_per_block(c.L) : ntt::Launch<uint64_t>::pairs_per_block(c.L);
+        const long long per = 2LL * ppb;
+        for (long long i = 0; i < (long long)c.count; i += per)
+            items.push_back(ntt::WorkItem{c.L, 0, (long long)c.off + i, std::min<long long>(per, (long long)c.count - i)});
+        const void *tw = ntt_plan_twiddles(c.plan);
+        unsigned char *slot = &cls[(size_t)c.L * cps];
+        memcpy(slot, &tw, sizeof tw);
+        ntt_plan_modc(c.plan, slot + sizeof(void *), cps - sizeof(void *));
+        b->persist_smem = std::max(b->persist_smem, ntt_full_smem(b->word, c.L));
+    }
+    b->nitems = (int)items.size();
+    if (b->nitems) {
+        if (cudaMalloc(&b->items, items.size() * sizeof(ntt::WorkItem)) != cudaSuccess ||
+            cudaMalloc(&b->counter, sizeof(int)) != cudaSuccess)
+            return bail(ntt_fail(NTT_ERR_OOM, "ntt_batch_plan: work list"));
+        if (cudaMemcpy(b->items, items.data(), items.size() * sizeof(ntt::WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ntt_fail(NTT_ERR_CUDA, "ntt_batch_plan: upload work list"));
+        b->persist_grid = std::min(ntt_num_sms(), b->nitems);
+    }
+    const int K = (int)std::min<size_t>(4, nsplit + (b->nitems ? 1 : 0));
+    if (K == 0) return bail(ntt_fail(NTT_ERR_ARG, "ntt_batch_plan: empty batch"));
+    std::vector<double> load(K, 0.0);
+    const int first = (b->nitems && K > 1) ? 1 : 0;          // stream 0 carries the persistent launch
+    for (auto &c : b->classes) {
+        if (c.stream == -1) { load[0] += c.work; continue; }
+        int best = first;
+        for (int i = first; i < K; ++i)
+            if (load[i] < load[best]) best = i;
         c.stream = best;
         load[best] += c.work;
     }
@@ -163,7 +212,13 @@ extern "C" ntt_status ntt_batch_exec(ntt_batch_t b, ntt_stream_t stream)
     if (cudaEventRecord(b->fork, user) != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec: record");
     for (auto s : b->streams)
         if (cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec: wait");
+    if (b->nitems) {
+        ntt_status s = ntt_launch_persistent(b->word, b->descs, b->items, b->nitems, b->counter, b->cls.data(),
+                                             b->persist_lmax, b->persist_grid, b->persist_smem, b->streams[0]);
+        if (s != NTT_OK) return s;
+    }
     for (auto &c : b->classes) {
+        if (c.stream < 0) continue;                       // in the persistent launch
         cudaStream_t st = b->streams[c.stream];
         const unsigned char *d = (const unsigned char *)b->descs + c.off * 3 * sizeof(void *);
         ntt_status s = ntt_conv_descs(c.plan, d, (long long)c.count, c.scratch, c.wave, st);

@@ -64,7 +64,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 // At the start of each pair one thread asks the copy engine to bring the
 // next pair's f and g into L2, so their loads do not wait on HBM.
 template <typename W, int L, int SRC>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
+__device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long base, long long end, long long stride)
 {
     using G = Geo<W, L>;
     constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, L>::GPC;
@@ -89,12 +89,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
             fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
         }
     };
-    const long long stride = (long long)gridDim.x * GPC;
-    for (long long rho = (long long)blockIdx.x * GPC + gid; rho < a.nrows; rho += stride) {
+    for (long long rho = base + gid; rho < end; rho += stride) {
         const W *fp, *gp;
         W *hp;
         ptrs(rho, fp, gp, hp);
-        if (tau == 0 && rho + stride < a.nrows) {
+        if (tau == 0 && rho + stride < end) {
             const W *fn, *gn;
             W *hn;
             ptrs(rho + stride, fn, gn, hn);
@@ -117,6 +116,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
             hp[(N - x) & (N - 1u)] = canon<W>(v[0][k], (W)1, a.c.onep, a.c.m);
         }
     }
+}
+
+template <typename W, int L, int SRC>
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
+{
+    constexpr int GPC = RowShape<W, L, L>::GPC;
+    conv_fused_body<W, L, SRC>(a, (long long)blockIdx.x * GPC, a.nrows, (long long)gridDim.x * GPC);
 }
 
 // ---- column/row fused kernel ---------------------------------------------
@@ -289,7 +295,7 @@ struct CRShape {
 // row and are read from the plan's table, the inverse ones do not and are
 // read from shared memory.
 template <typename W, int L, int LROW, int SRC>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
+__device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long end, long long stride)
 {
     using SH = CRShape<W, L, LROW>;
     using GR = typename SH::GR;
@@ -349,8 +355,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
 #pragma unroll
             for (int k = 0; k < RC; ++k) dst[j * RC + k] = src[ptau + (uint32_t)j * TPP + ((uint32_t)k << RW)];
     };
-    const long long stride = (long long)gridDim.x * PPC;
-    long long rho = (long long)blockIdx.x * PPC + pid;
+    long long rho = base + pid;
     W v[2][R];
     const W *fp = nullptr, *gp = nullptr;
     W *hp = nullptr;
@@ -358,11 +363,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
     // (split rows keep no prefetched registers across their inverse: it reads
     // its twiddles from global memory and needs the registers itself)
     constexpr bool PREF = FULL;
-    if (PREF && rho < a.nrows) {
+    if (PREF && rho < end) {
         ptrs(rho, fp, gp, hp, rowoff);
         load_cols(fp, v[1]);
     }
-    for (; rho < a.nrows; rho += stride) {
+    for (; rho < end; rho += stride) {
         if (!PREF) {
             ptrs(rho, fp, gp, hp, rowoff);
             load_cols(fp, v[1]);
@@ -370,7 +375,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
         W *const hcur = hp;
         const uint32_t rcur = rowoff;
         const W *gcur = gp;
-        if (ptau == 0 && rho + stride < a.nrows) {
+        if (ptau == 0 && rho + stride < end) {
             const W *fn, *gn;
             W *hn;
             uint32_t ro;
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
         fwd_all<W, L, RW, 0, 2, FTW>(v, rcur + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[1][k], v[0][k], a.c);
-        if (PREF && rho + stride < a.nrows) {
+        if (PREF && rho + stride < end) {
             ptrs(rho + stride, fp, gp, hp, rowoff);
             load_cols(fp, v[1]);                            // next row's f
         }
@@ -431,6 +436,78 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
                 if constexpr (FULL) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
                 else hcur[x] = v[0][j * RC + k];
             }
+    }
+}
+
+template <typename W, int L, int LROW, int SRC>
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
+{
+    constexpr int PPC = CRShape<W, L, LROW>::PPC;
+    conv_cr_body<W, L, LROW, SRC>(a, (long long)blockIdx.x * PPC, a.nrows, (long long)gridDim.x * PPC);
+}
+
+// ---- one persistent launch for every whole-sequence length of a batch ----
+//
+// Work items {log2 N, first pair, count} of a batch plan's descriptor list
+// (grouped by length) are pulled by the blocks with an atomic counter; a
+// block runs the item with the fused body of its length, staging that
+// length's twiddle table into shared memory first.  Blocks never wait on
+// one another.
+
+struct WorkItem {
+    int L;
+    int reserved;
+    long long first;
+    long long count;
+};
+
+template <typename W> struct ClassParam {
+    const W *tw;
+    ModC<W> c;
+};
+
+// The per-length constants travel by value in the kernel's parameter space,
+// so each length's body reads them as constant-bank operands (as the
+// single-length kernels do) instead of holding them in registers.
+template <typename W> struct PersistArgs {
+    const DevDesc<W> *descs;
+    const WorkItem *items;
+    int nitems;
+    int *counter;                      // zeroed before each launch
+    ClassParam<W> cls[LRMax<W>::v + 1];  // indexed by log2 N
+};
+
+template <typename W, int L>
+__device__ __forceinline__ void persist_item(const PersistArgs<W> &a, const WorkItem &w)
+{
+    constexpr int RW = Arith<W>::RB + 5;
+    RowArgs<W> ra{nullptr, nullptr, nullptr, a.descs, 0, 0, a.cls[L].tw, a.cls[L].c};
+    if constexpr (L <= RW) conv_fused_body<W, L, 1>(ra, w.first, w.first + w.count, RowShape<W, L, L>::GPC);
+    else conv_cr_body<W, L, L, 1>(ra, w.first, w.first + w.count, CRShape<W, L, L>::PPC);
+}
+
+template <typename W, int L, int HI>
+__device__ __forceinline__ void persist_dispatch(const PersistArgs<W> &a, const WorkItem &w)
+{
+    if constexpr (L <= HI) {
+        if (w.L == L) persist_item<W, L>(a, w);
+        else persist_dispatch<W, L + 1, HI>(a, w);
+    }
+}
+
+// HI: the longest length the kernel is compiled for (the one-warp lengths
+// only, or every whole-sequence length).
+template <typename W, int HI>
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_persistent(PersistArgs<W> a)
+{
+    __shared__ int item;
+    for (;;) {
+        __syncthreads();                                   // previous item done with shared memory
+        if (threadIdx.x == 0) item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int it = item;
+        if (it >= a.nitems) break;
+        persist_dispatch<W, 0, HI>(a, a.items[it]);
     }
 }
 

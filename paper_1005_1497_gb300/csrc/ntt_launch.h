@@ -30,6 +30,11 @@ template <typename W> struct Launch {
                              const ModC<W> &c, int grid, cudaStream_t st);
     static cudaError_t check_range(const W *data, long long n, W m, unsigned long long *bad, int grid,
                                    cudaStream_t st);
+    // dynamic shared memory of the whole-sequence fused kernel of length 2^L
+    static size_t conv_full_smem(int L);
+    // one persistent launch over a work list of whole-sequence items
+    // (lmax: the longest length among the items; selects the instantiation)
+    static cudaError_t conv_persistent(const PersistArgs<W> &a, int lmax, int grid, size_t smem, cudaStream_t st);
 };
 
 }  // namespace ntt

@@ -184,6 +184,56 @@ def test_conv_batched_uneven(ntt, orc):
     bp.close()
 
 
+@pytest.mark.parametrize("m,word,lmax", [(M, 32, None), (M, 32, 14), (M64, 64, None), (M64, 64, 13)])
+def test_conv_batched_persistent(ntt, orc, monkeypatch, m, word, lmax):
+    """Whole-sequence lengths of a batch plan run in one persistent launch
+    whose blocks pull work items from a counter: many short pairs of every
+    length up to one block's, some computed in place (h = f), executed
+    eagerly twice and by graph replay twice (the counter is re-armed)."""
+    from paper_1005_1497_gb300 import inputs
+    if lmax is not None:
+        monkeypatch.setenv("NTT_PERSIST_LMAX", str(lmax))
+    top = 14 if word == 32 else 13
+    lens = inputs.log_uniform_lengths(700, 0, top, seed=11 + word)
+    dt = torch.int32 if word == 32 else torch.int64
+    triples, ref = [], []
+    for i, N in enumerate(lens):
+        N = int(N)
+        f, g = pairs(m, 1, N, seed=900 + i)
+        fd = dev(f[0], word)
+        h = fd if i % 5 == 0 else torch.empty(N, dtype=dt, device="cuda")
+        triples.append((fd, dev(g[0], word), h))
+        ref.append((f[0], g[0], N))
+    f_keep = [(i, host(t[0]).copy()) for i, t in enumerate(triples) if i % 5 == 0]
+    bp = ntt.BatchPlan(m, triples)
+    bp.exec()
+    torch.cuda.synchronize()
+    want = []
+    for (f, g, N), (_, _, h) in zip(ref, triples):
+        hh = host(h)
+        if N <= 512:
+            assert np.array_equal(hh, orc.conv(f, g, m)), N
+        else:
+            idx = np.random.default_rng(N).integers(0, N, 16, dtype=np.uint64)
+            assert np.array_equal(hh[idx.astype(np.int64)], orc.conv_sample(f, g, m, idx)), N
+        want.append(hh.copy())
+    # restore the in-place inputs, then repeat eagerly and by graph replay
+    for rep in range(4):
+        for i, fk in f_keep:
+            triples[i][0].copy_(torch.from_numpy(fk.astype(np.int32 if word == 32 else np.int64)))
+        for i, (_, _, h) in enumerate(triples):
+            if i % 5:
+                h.zero_()
+        if rep < 2:
+            bp.exec()
+        else:
+            bp.exec_graph()
+        torch.cuda.synchronize()
+        for w, (_, _, h) in zip(want, triples):
+            assert np.array_equal(host(h), w)
+    bp.close()
+
+
 def test_check_range(ntt):
     plan = ntt.Plan(M, 1 << 10)
     x = torch.zeros(5000, dtype=torch.int32, device="cuda")
