@@ -76,7 +76,16 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")
         os.replace(tmp, LIB)
+    _prune(objs)
     return LIB
+
+
+def _prune(keep) -> None:
+    """Drop cached objects of earlier source versions."""
+    keep = {os.path.basename(o) for o in keep}
+    for name in os.listdir(BUILD):
+        if name.endswith(".o") and name not in keep:
+            os.remove(os.path.join(BUILD, name))
 
 
 
