@@ -419,15 +419,6 @@ ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, voi
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (scratch)");
 }
 
-const void *ntt_plan_twiddles(ntt_plan_t p) { return p ? p->tw : nullptr; }
-
-void ntt_plan_modc(ntt_plan_t p, void *out, size_t bytes)
-{
-    if (!p || !out) return;
-    if (p->word == 32) memcpy(out, &p->c32, std::min(bytes, sizeof p->c32));
-    else memcpy(out, &p->c64, std::min(bytes, sizeof p->c64));
-}
-
 // Longest length a batch plan folds into its persistent launch: the
 // one-warp lengths by default (their bodies share one kernel without
 // spilling); NTT_PERSIST_LMAX raises it to every whole-sequence length.
@@ -447,18 +438,34 @@ size_t ntt_full_smem(int word_bits, int log2N)
 
 int ntt_num_sms() { return num_sms(); }
 
+// One RowArgs per length: the batch's descriptor list, and the plan's
+// twiddle table and constants (a null table marks an absent length).
+template <typename W>
+static void fill_persist_classes(ntt::PersistArgs<W> &a, const void *descs, const ntt_plan_t *plans)
+{
+    for (int L = 0; L <= ntt::LRMax<W>::v; ++L) {
+        RowArgs<W> &r = a.cls[L];
+        r = RowArgs<W>{};
+        r.descs = (const DevDesc<W> *)descs;
+        if (!plans[L]) continue;
+        r.tw = (const W *)plans[L]->tw;
+        if constexpr (sizeof(W) == 4) r.c = plans[L]->c32;
+        else r.c = plans[L]->c64;
+    }
+}
+
 ntt_status ntt_launch_persistent(int word_bits, const void *descs, const void *items, int nitems, int *counter,
-                                 const void *cls, int lmax, int grid, size_t smem, cudaStream_t st)
+                                 const ntt_plan_t *plans, int lmax, int grid, size_t smem, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e == cudaSuccess) {
         if (word_bits == 32) {
-            ntt::PersistArgs<uint32_t> a{(const DevDesc<uint32_t> *)descs, (const ntt::WorkItem *)items, nitems, counter, {}};
-            memcpy(a.cls, cls, sizeof a.cls);
+            ntt::PersistArgs<uint32_t> a{(const ntt::WorkItem *)items, nitems, counter, {}};
+            fill_persist_classes(a, descs, plans);
             e = Launch<uint32_t>::conv_persistent(a, lmax, grid, smem, st);
         } else {
-            ntt::PersistArgs<uint64_t> a{(const DevDesc<uint64_t> *)descs, (const ntt::WorkItem *)items, nitems, counter, {}};
-            memcpy(a.cls, cls, sizeof a.cls);
+            ntt::PersistArgs<uint64_t> a{(const ntt::WorkItem *)items, nitems, counter, {}};
+            fill_persist_classes(a, descs, plans);
             e = Launch<uint64_t>::conv_persistent(a, lmax, grid, smem, st);
         }
     }

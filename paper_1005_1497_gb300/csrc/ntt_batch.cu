@@ -60,7 +60,7 @@ struct ntt_batch_s {
     // whole-sequence lengths: one persistent launch over a work list
     void *items = nullptr;           // ntt::WorkItem[nitems]
     int nitems = 0;
-    std::vector<unsigned char> cls;  // host copy of ntt::ClassParam<W>[LR_max + 1], passed by value
+    std::vector<ntt_plan_t> persist_plans;   // indexed by log2 N; null where absent
     int *counter = nullptr;
     size_t persist_smem = 0;
     int persist_grid = 0;
@@ -153,9 +153,7 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
     const int lrmax = b->word == 32 ? ntt::LRMax<uint32_t>::v : ntt::LRMax<uint64_t>::v;
     const int plmax = ntt_persist_lmax(b->word);
     std::vector<ntt::WorkItem> items;
-    std::vector<unsigned char> &cls = b->cls;
-    cls.assign((size_t)(lrmax + 1) * std::max(sizeof(ntt::ClassParam<uint32_t>), sizeof(ntt::ClassParam<uint64_t>)), 0);
-    const size_t cps = b->word == 32 ? sizeof(ntt::ClassParam<uint32_t>) : sizeof(ntt::ClassParam<uint64_t>);
+    b->persist_plans.assign(lrmax + 1, nullptr);
     size_t nsplit = 0;             // classes with their own launches
     for (auto &c : b->classes) {
         if (c.L > plmax) { ++nsplit; continue; }
@@ -165,10 +163,7 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
         const long long per = 2LL * ppb;
         for (long long i = 0; i < (long long)c.count; i += per)
             items.push_back(ntt::WorkItem{c.L, 0, (long long)c.off + i, std::min<long long>(per, (long long)c.count - i)});
-        const void *tw = ntt_plan_twiddles(c.plan);
-        unsigned char *slot = &cls[(size_t)c.L * cps];
-        memcpy(slot, &tw, sizeof tw);
-        ntt_plan_modc(c.plan, slot + sizeof(void *), cps - sizeof(void *));
+        b->persist_plans[c.L] = c.plan;
         b->persist_smem = std::max(b->persist_smem, ntt_full_smem(b->word, c.L));
     }
     b->nitems = (int)items.size();
@@ -213,7 +208,7 @@ extern "C" ntt_status ntt_batch_exec(ntt_batch_t b, ntt_stream_t stream)
     for (auto s : b->streams)
         if (cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec: wait");
     if (b->nitems) {
-        ntt_status s = ntt_launch_persistent(b->word, b->descs, b->items, b->nitems, b->counter, b->cls.data(),
+        ntt_status s = ntt_launch_persistent(b->word, b->descs, b->items, b->nitems, b->counter, b->persist_plans.data(),
                                              b->persist_lmax, b->persist_grid, b->persist_smem, b->streams[0]);
         if (s != NTT_OK) return s;
     }

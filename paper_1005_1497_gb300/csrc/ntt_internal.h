@@ -22,12 +22,10 @@ ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, voi
 uint32_t ntt_tuned_wave(int word_bits, int log2N);
 // Device twiddle table of a plan, and its arithmetic constants (ModC<W> of
 // the plan's word size copied to out, `bytes` bytes).
-const void *ntt_plan_twiddles(ntt_plan_t p);
-void ntt_plan_modc(ntt_plan_t p, void *out, size_t bytes);
 // One persistent launch of the whole-sequence fused bodies over a work list
 // (device pointers: descs, items, counter (zeroed here), class params).
 ntt_status ntt_launch_persistent(int word_bits, const void *descs, const void *items, int nitems, int *counter,
-                                 const void *cls_host, int lmax, int grid, size_t smem, cudaStream_t st);   // cls_host: ClassParam<W>[LR_max+1], copied into the launch
+                                 const ntt_plan_t *plans, int lmax, int grid, size_t smem, cudaStream_t st);   // plans: indexed by log2 N, null where absent
 size_t ntt_full_smem(int word_bits, int log2N);
 int ntt_persist_lmax(int word_bits);   // longest length a batch plan runs in its persistent launch
 int ntt_num_sms();

@@ -63,8 +63,9 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 // the decimation-in-time inverse; results are stored canonical at <-x>_N.
 // At the start of each pair one thread asks the copy engine to bring the
 // next pair's f and g into L2, so their loads do not wait on HBM.
+// Rows [base + group, a.nrows) by steps of stride.
 template <typename W, int L, int SRC>
-__device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long base, long long end, long long stride)
+__device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long base, long long stride)
 {
     using G = Geo<W, L>;
     constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, L>::GPC;
@@ -89,11 +90,11 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
             fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
         }
     };
-    for (long long rho = base + gid; rho < end; rho += stride) {
+    for (long long rho = base + gid; rho < a.nrows; rho += stride) {
         const W *fp, *gp;
         W *hp;
         ptrs(rho, fp, gp, hp);
-        if (tau == 0 && rho + stride < end) {
+        if (tau == 0 && rho + stride < a.nrows) {
             const W *fn, *gn;
             W *hn;
             ptrs(rho + stride, fn, gn, hn);
@@ -119,10 +120,10 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
 }
 
 template <typename W, int L, int SRC>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(RowArgs<W> a)
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(const __grid_constant__ RowArgs<W> a)
 {
     constexpr int GPC = RowShape<W, L, L>::GPC;
-    conv_fused_body<W, L, SRC>(a, (long long)blockIdx.x * GPC, a.nrows, (long long)gridDim.x * GPC);
+    conv_fused_body<W, L, SRC>(a, (long long)blockIdx.x * GPC, (long long)gridDim.x * GPC);
 }
 
 // ---- column/row fused kernel ---------------------------------------------
@@ -294,8 +295,9 @@ struct CRShape {
 // the wave's scratch; the forward node twiddles of such a row depend on the
 // row and are read from the plan's table, the inverse ones do not and are
 // read from shared memory.
-template <typename W, int L, int LROW, int SRC>
-__device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long end, long long stride)
+// Rows [base + row group, end) by steps of stride; end is a.nrows unless ITEM.
+template <typename W, int L, int LROW, int SRC, bool ITEM = false>
+__device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long stride, long long end = 0)
 {
     using SH = CRShape<W, L, LROW>;
     using GR = typename SH::GR;
@@ -363,11 +365,11 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
     // (split rows keep no prefetched registers across their inverse: it reads
     // its twiddles from global memory and needs the registers itself)
     constexpr bool PREF = FULL;
-    if (PREF && rho < end) {
+    if (PREF && rho < (ITEM ? end : a.nrows)) {
         ptrs(rho, fp, gp, hp, rowoff);
         load_cols(fp, v[1]);
     }
-    for (; rho < end; rho += stride) {
+    for (; rho < (ITEM ? end : a.nrows); rho += stride) {
         if (!PREF) {
             ptrs(rho, fp, gp, hp, rowoff);
             load_cols(fp, v[1]);
@@ -375,7 +377,7 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
         W *const hcur = hp;
         const uint32_t rcur = rowoff;
         const W *gcur = gp;
-        if (ptau == 0 && rho + stride < end) {
+        if (ptau == 0 && rho + stride < (ITEM ? end : a.nrows)) {
             const W *fn, *gn;
             W *hn;
             uint32_t ro;
@@ -407,7 +409,7 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
         fwd_all<W, L, RW, 0, 2, FTW>(v, rcur + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[1][k], v[0][k], a.c);
-        if (PREF && rho + stride < end) {
+        if (PREF && rho + stride < (ITEM ? end : a.nrows)) {
             ptrs(rho + stride, fp, gp, hp, rowoff);
             load_cols(fp, v[1]);                            // next row's f
         }
@@ -440,10 +442,10 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
 }
 
 template <typename W, int L, int LROW, int SRC>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(RowArgs<W> a)
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(const __grid_constant__ RowArgs<W> a)
 {
     constexpr int PPC = CRShape<W, L, LROW>::PPC;
-    conv_cr_body<W, L, LROW, SRC>(a, (long long)blockIdx.x * PPC, a.nrows, (long long)gridDim.x * PPC);
+    conv_cr_body<W, L, LROW, SRC>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC);
 }
 
 // ---- one persistent launch for every whole-sequence length of a batch ----
@@ -461,29 +463,30 @@ struct WorkItem {
     long long count;
 };
 
-template <typename W> struct ClassParam {
-    const W *tw;
-    ModC<W> c;
-};
-
-// The per-length constants travel by value in the kernel's parameter space,
-// so each length's body reads them as constant-bank operands (as the
-// single-length kernels do) instead of holding them in registers.
+// The per-length arguments (descriptor list, twiddle table, constants) travel
+// by value in the kernel's parameter space, so each length's body reads them
+// as constant-bank operands, as the single-length kernels do, instead of
+// holding them in registers.
 template <typename W> struct PersistArgs {
-    const DevDesc<W> *descs;
     const WorkItem *items;
     int nitems;
     int *counter;                      // zeroed before each launch
-    ClassParam<W> cls[LRMax<W>::v + 1];  // indexed by log2 N
+    RowArgs<W> cls[LRMax<W>::v + 1];   // indexed by log2 N
 };
 
 template <typename W, int L>
 __device__ __forceinline__ void persist_item(const PersistArgs<W> &a, const WorkItem &w)
 {
     constexpr int RW = Arith<W>::RB + 5;
-    RowArgs<W> ra{nullptr, nullptr, nullptr, a.descs, 0, 0, a.cls[L].tw, a.cls[L].c};
-    if constexpr (L <= RW) conv_fused_body<W, L, 1>(ra, w.first, w.first + w.count, RowShape<W, L, L>::GPC);
-    else conv_cr_body<W, L, L, 1>(ra, w.first, w.first + w.count, CRShape<W, L, L>::PPC);
+    // rows [first, first + count) of the descriptor list; the one-warp body
+    // takes them as a local copy of its arguments with nrows set (it compiles
+    // without spills that way), the column/row body as an explicit bound
+    if constexpr (L <= RW) {
+        RowArgs<W> ra = a.cls[L];
+        ra.nrows = w.first + w.count;
+        conv_fused_body<W, L, 1>(ra, w.first, RowShape<W, L, L>::GPC);
+    }
+    else conv_cr_body<W, L, L, 1, true>(a.cls[L], w.first, CRShape<W, L, L>::PPC, w.first + w.count);
 }
 
 template <typename W, int L, int HI>
@@ -498,7 +501,7 @@ __device__ __forceinline__ void persist_dispatch(const PersistArgs<W> &a, const 
 // HI: the longest length the kernel is compiled for (the one-warp lengths
 // only, or every whole-sequence length).
 template <typename W, int HI>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_persistent(PersistArgs<W> a)
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_persistent(const __grid_constant__ PersistArgs<W> a)
 {
     __shared__ int item;
     for (;;) {
@@ -524,7 +527,7 @@ template <typename W> struct NttArgs {
 };
 
 template <typename W, int L, bool INV>
-__global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(NttArgs<W> a)
+__global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(const __grid_constant__ NttArgs<W> a)
 {
     using G = Geo<W, L>;
     constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, L>::GPC;
@@ -629,7 +632,7 @@ __device__ __forceinline__ void col_fwd_levels(W (&v)[1 << (L - LR)], const W *_
 }
 
 template <typename W, int L, int LR, int NS, int SRC>
-__global__ void __launch_bounds__(256) k_cols_fwd(ColArgs<W> a)
+__global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int RC = 1 << (L - LR);
     constexpr uint32_t N = 1u << L;
@@ -661,7 +664,7 @@ __global__ void __launch_bounds__(256) k_cols_fwd(ColArgs<W> a)
 // Inputs < 2m; then the output stage: index <-x>_N, canonical residue.
 // DST 0: contiguous out; 1: descriptor h.
 template <typename W, int L, int LR, int DST>
-__global__ void __launch_bounds__(256) k_cols_inv(ColArgs<W> a)
+__global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int LC = L - LR, RC = 1 << LC;
     constexpr uint32_t N = 1u << L;
@@ -686,7 +689,7 @@ __global__ void __launch_bounds__(256) k_cols_inv(ColArgs<W> a)
 
 // Forward row levels of the split path (single sequence, in place in scratch).
 template <typename W, int L, int LR>
-__global__ void __launch_bounds__(BLOCK, 1) k_rows_fwd(RowArgs<W> a)
+__global__ void __launch_bounds__(BLOCK, 1) k_rows_fwd(const __grid_constant__ RowArgs<W> a)
 {
     using G = Geo<W, LR>;
     constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, LR>::GPC;
