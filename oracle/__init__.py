@@ -33,6 +33,7 @@ _lock = threading.Lock()
 _lib = None
 
 _U64P = ctypes.POINTER(ctypes.c_uint64)
+_I64P = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False, out: str | None = None, defines: dict | None = None) -> str:
@@ -67,6 +68,15 @@ def _bind(lib):
         fn = getattr(lib, name)
         fn.restype = ctypes.c_int
         fn.argtypes = [p, p, p, u64, u64, u64]
+    ip = _I64P
+    lib.or_int_conv.restype = ctypes.c_int
+    lib.or_int_conv.argtypes = [ip, ip, ip, u64]
+    lib.or_int_conv_sample.restype = ctypes.c_int
+    lib.or_int_conv_sample.argtypes = [ip, ip, u64, p, u64, ip]
+    lib.or_dyadic_ntt.restype = ctypes.c_int
+    lib.or_dyadic_ntt.argtypes = [p, p, u64, u64, u64]
+    lib.or_dyadic_conv.restype = ctypes.c_int
+    lib.or_dyadic_conv.argtypes = [p, p, p, u64, u64]
     return lib
 
 
@@ -170,6 +180,50 @@ class Oracle:
         g, pg = self._arr(g)
         h = np.empty_like(f)
         rc = fn(pf, pg, h.ctypes.data_as(_U64P), f.shape[-1], m, w)
+        if rc:
+            raise RuntimeError(f"oracle call failed ({rc})")
+        return h
+
+
+    # --- exact integer convolution (Eq. 1, no modulus) -----------------
+    @staticmethod
+    def _iarr(x):
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.int64))
+        return a, a.ctypes.data_as(_I64P)
+
+    def int_conv(self, f, g):
+        """Exact h(j) = sum_k f(k) g(<j-k>_N) for signed 64-bit inputs.
+        Raises OverflowError if some h(j) does not fit a signed 64-bit word."""
+        f, pf = self._iarr(f)
+        g, pg = self._iarr(g)
+        h = np.empty_like(f)
+        if self.lib.or_int_conv(pf, pg, h.ctypes.data_as(_I64P), f.shape[-1]):
+            raise OverflowError("exact convolution exceeds 64 bits")
+        return h
+
+    def int_conv_sample(self, f, g, idx):
+        f, pf = self._iarr(f)
+        g, pg = self._iarr(g)
+        idx, pi = self._arr(idx)
+        out = np.empty(idx.shape[0], dtype=np.int64)
+        if self.lib.or_int_conv_sample(pf, pg, f.shape[-1], pi, idx.shape[0], out.ctypes.data_as(_I64P)):
+            raise OverflowError("exact convolution exceeds 64 bits")
+        return out
+
+    # --- modulus-free transform mod 2^alpha (Sec. III-B) ----------------
+    def dyadic_ntt(self, x, alpha, a):
+        x, px = self._arr(x)
+        X = np.empty_like(x)
+        rc = self.lib.or_dyadic_ntt(px, X.ctypes.data_as(_U64P), x.shape[-1], alpha, a)
+        if rc:
+            raise RuntimeError(f"oracle call failed ({rc})")
+        return X
+
+    def dyadic_conv(self, f, g, alpha):
+        f, pf = self._arr(f)
+        g, pg = self._arr(g)
+        h = np.empty_like(f)
+        rc = self.lib.or_dyadic_conv(pf, pg, h.ctypes.data_as(_U64P), f.shape[-1], alpha)
         if rc:
             raise RuntimeError(f"oracle call failed ({rc})")
         return h

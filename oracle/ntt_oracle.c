@@ -20,6 +20,9 @@
  *   - a textbook radix-2 Cooley-Tukey convolution, with e^{2 pi i a/N}
  *     replaced by powers of the integer root (Sec. I), for lengths where
  *     the O(N^2) definitions are too slow; it is pinned against them.
+ *   - the exact integer circular convolution (Eq. 1 with no modulus),
+ *     accumulated in signed __int128
+ *   - the modulus-free transform and convolution modulo 2^alpha (Sec. III-B)
  *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes of the repository):
@@ -299,5 +302,88 @@ int or_fast_ntt(const uint64_t *x, uint64_t *X, uint64_t N, uint64_t m, uint64_t
     for (uint64_t i = 0; i < N; i++)
         X[i] = x[i] % m;
     radix2_transform(X, N, m, w);
+    return 0;
+}
+
+/* ---- Exact integer circular convolution -------------------------------
+ * Eq. 1 without the modulus: h(j) = sum_k f(k) g(<j-k>_N) over the
+ * integers, accumulated in signed __int128 (the "exact digital filtering"
+ * that Sec. I and the Conclusion aim at; recovering it from residues is the
+ * Chinese remainder theorem, which this oracle does not use).  Inputs are
+ * signed 64-bit.  Returns 0 when every h(j) fits a signed 64-bit word, -1
+ * otherwise (h then holds the low 64 bits). */
+typedef __int128 i128;
+
+static int int_conv_at(const int64_t *f, const int64_t *g, uint64_t N, uint64_t j, int64_t *out)
+{
+    i128 acc = 0;
+    for (uint64_t k = 0; k < N; k++) {
+        uint64_t idx = (j + N - k) % N;                         /* <j-k>_N */
+        acc += (i128)f[k] * (i128)g[idx];
+    }
+    *out = (int64_t)acc;
+    return (acc >= -(((i128)1) << 63) && acc < (((i128)1) << 63)) ? 0 : -1;
+}
+
+int or_int_conv(const int64_t *f, const int64_t *g, int64_t *h, uint64_t N)
+{
+    int rc = 0;
+    for (uint64_t j = 0; j < N; j++)
+        rc |= int_conv_at(f, g, N, j, &h[j]);
+    return rc;
+}
+
+int or_int_conv_sample(const int64_t *f, const int64_t *g, uint64_t N, const uint64_t *idx, uint64_t count,
+                       int64_t *out)
+{
+    int rc = 0;
+    for (uint64_t i = 0; i < count; i++)
+        rc |= int_conv_at(f, g, N, idx[i] % N, &out[i]);
+    return rc;
+}
+
+/* ---- Modulus-free transform (Sec. III-B) --------------------------------
+ * For odd a, a^{2^{alpha-2}} = 1 mod 2^alpha (Eq. Dyadic), so powers of a
+ * give a length-N kernel modulo 2^alpha with no division: arithmetic wraps
+ * at 2^64 and truncation to alpha bits is the residue.  1 <= alpha <= 64.
+ *   X(u) = < sum_t x(t) a^{<ut>_N} >_{2^alpha}           (Eq. 2 with m = 2^alpha)
+ *   h(j) = < sum_k f(k) g(<j-k>_N) >_{2^alpha}           (Eq. 1 with m = 2^alpha) */
+static uint64_t low_bits(uint64_t v, uint64_t alpha)
+{
+    return alpha >= 64 ? v : (v & ((((uint64_t)1) << alpha) - 1));
+}
+
+int or_dyadic_ntt(const uint64_t *x, uint64_t *X, uint64_t N, uint64_t alpha, uint64_t a)
+{
+    if (alpha < 1 || alpha > 64 || N == 0)
+        return -2;
+    uint64_t *pw = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    if (!pw)
+        return -1;
+    uint64_t p = 1;
+    for (uint64_t k = 0; k < N; k++) {
+        pw[k] = low_bits(p, alpha);
+        p *= a;                                                 /* wraps at 2^64 */
+    }
+    for (uint64_t u = 0; u < N; u++) {
+        uint64_t acc = 0;
+        for (uint64_t t = 0; t < N; t++)
+            acc += x[t] * pw[(uint64_t)(((u128)u * t) % N)];
+        X[u] = low_bits(acc, alpha);
+    }
+    free(pw);
+    return 0;
+}
+
+int or_dyadic_conv(const uint64_t *f, const uint64_t *g, uint64_t *h, uint64_t N, uint64_t alpha)
+{
+    if (alpha < 1 || alpha > 64)
+        return -2;
+    for (uint64_t j = 0; j < N; j++) {
+        uint64_t acc = 0;
+        for (uint64_t k = 0; k < N; k++)
+            acc += f[k] * g[(j + N - k) % N];
+        h[j] = low_bits(acc, alpha);
+    }
     return 0;
 }
