@@ -318,7 +318,11 @@ static int int_conv_at(const int64_t *f, const int64_t *g, uint64_t N, uint64_t 
 {
     i128 acc = 0;
     for (uint64_t k = 0; k < N; k++) {
+#if ORACLE_MUTANT == 6
+        uint64_t idx = (j + k) % N;                             /* wrong index sign */
+#else
         uint64_t idx = (j + N - k) % N;                         /* <j-k>_N */
+#endif
         acc += (i128)f[k] * (i128)g[idx];
     }
     *out = (int64_t)acc;
@@ -369,7 +373,11 @@ int or_dyadic_ntt(const uint64_t *x, uint64_t *X, uint64_t N, uint64_t alpha, ui
         uint64_t acc = 0;
         for (uint64_t t = 0; t < N; t++)
             acc += x[t] * pw[(uint64_t)(((u128)u * t) % N)];
+#if ORACLE_MUTANT == 7
+        X[u] = acc;                                             /* not truncated to alpha bits */
+#else
         X[u] = low_bits(acc, alpha);
+#endif
     }
     free(pw);
     return 0;
