@@ -294,6 +294,55 @@ void ntt_server_destroy(ntt_server_t srv);
 ntt_status conv_circular_noalloc(ntt_plan_t plan, const void *f_dev, const void *g_dev, void *h_dev,
                                  size_t batch, ntt_stream_t stream);
 
+/* ---------------------------------------------- exact integer convolution */
+
+/* Exact (non-modular) circular convolution of signed 64-bit sequences,
+ *     h(j) = sum_k f(k) g(<j-k>_N)   over the integers       (Eq. 1, no modulus)
+ * -- the exact digital filtering of Sec. I -- from the modular convolutions
+ * of several Rader primes (prime factors of Fermat numbers, Sec. III-A /
+ * Table 1, whose multiplicative order of 2 the length N divides) and the
+ * Chinese remainder theorem. */
+#define NTT_EXACT_MAX_PRIMES 4
+
+typedef struct ntt_exact_s *ntt_exact_t;          /* opaque, owned by the library */
+
+typedef struct {
+    uint32_t N;
+    uint32_t bound_bits;            /* the caller's bound: every |h(j)| < 2^bound_bits */
+    uint32_t nprimes;               /* primes used (<= NTT_EXACT_MAX_PRIMES) */
+    uint32_t word_bits[NTT_EXACT_MAX_PRIMES];
+    uint32_t reserved;
+    uint64_t primes[NTT_EXACT_MAX_PRIMES];
+    double capacity_bits;           /* log2 of the product M of the primes (> bound_bits + 1) */
+    uint64_t wave;                  /* pairs per scratch wave */
+} ntt_exact_info_t;
+
+/* Plan exact convolutions of length N (a power of two) whose outputs all
+ * satisfy |h(j)| < 2^bound_bits, 1 <= bound_bits <= 63 (e.g. bound_bits =
+ * log2 N + bits(max|f|) + bits(max|g|)).  The plan takes the cheapest primes
+ * (32-bit words first) whose product M reaches 2^(bound_bits + 1), creates
+ * one modular plan per prime and owns device scratch for a wave of pairs
+ * (at most 256 MiB of residues).
+ * Errors: NTT_ERR_ARG (NULL out), NTT_ERR_LENGTH (N not a power of two, or
+ * the primes that admit N cannot cover the bound), NTT_ERR_RANGE
+ * (bound_bits outside 1..63), NTT_ERR_OOM, NTT_ERR_CUDA. */
+ntt_status ntt_exact_plan(uint32_t N, uint32_t bound_bits, ntt_exact_t *out);
+
+/* Fill *info.  Errors: NTT_ERR_ARG. */
+ntt_status ntt_exact_get_info(ntt_exact_t plan, ntt_exact_info_t *info);
+
+/* h_dev[b][j] = sum_k f_dev[b][k] g_dev[b][<j-k>_N] for b < batch: signed
+ * 64-bit words, row-major [batch][N], device memory owned by the caller; h
+ * may alias neither f nor g.  Exact whenever the plan's bound holds; an
+ * output beyond it comes back as its residue modulo M in (-M/2, M/2].
+ * Asynchronous on `stream`; a plan serves one call at a time.
+ * Errors: NTT_ERR_ARG, NTT_ERR_CUDA. */
+ntt_status conv_exact(ntt_exact_t plan, const int64_t *f_dev, const int64_t *g_dev, int64_t *h_dev, size_t batch,
+                      ntt_stream_t stream);
+
+/* Release the plan, its modular plans and its scratch.  NULL is a no-op. */
+void ntt_exact_destroy(ntt_exact_t plan);
+
 /* ----------------------------------------------------------------- checks */
 
 /* Count the words of `count` words at data_dev (word size of the plan) that

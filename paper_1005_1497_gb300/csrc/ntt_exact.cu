@@ -1,0 +1,287 @@
+// ntt_exact.cu -- exact integer circular convolution (Eq. 1 with no
+// modulus): the "exact digital filtering" of Sec. I, obtained from the
+// modular convolutions of several Rader primes (Sec. III-A, Table 1 and
+// other prime factors of Fermat numbers) and the Chinese remainder theorem.
+//
+//   1. one elementwise pass splits the signed 64-bit inputs into residues
+//      modulo every prime of the plan;
+//   2. each prime's residues are convolved by the fused modular path
+//      (forward transform, pointwise product, inverse, Eq. 1-3);
+//   3. one elementwise pass rebuilds each output from its residues by
+//      Garner's mixed-radix form of the Chinese remainder theorem and maps
+//      it to the signed range (-M/2, M/2], M the product of the primes.
+//
+// The result is exact whenever every |h(j)| < 2^bound_bits, the bound the
+// caller declares; the plan picks primes whose product exceeds 2^(bound+1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ntt_gb300.h"
+#include "ntt_internal.h"
+#include "nt_host.h"
+
+namespace {
+
+constexpr int KMAX = NTT_EXACT_MAX_PRIMES;
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// Residue and reconstruction constants of one prime, passed by value.
+struct PrimeC {
+    uint64_t m;
+    uint64_t onep;        // floor(2^64 / m): Shoup quotient of the factor 1
+    uint64_t r64;         // 2^64 mod m
+    int word;             // 32 or 64
+    int pad;
+};
+
+struct ExactArgs {
+    int k;                          // number of primes
+    long long n;                    // elements
+    PrimeC p[KMAX];
+    uint64_t inv[KMAX][KMAX];       // inv[i][j] = m_i^-1 mod m_j (i < j)
+    uint64_t invp[KMAX][KMAX];      // floor(inv 2^64 / m_j)
+    unsigned long long half_lo, half_hi;   // (M - 1) / 2
+    unsigned long long M_lo, M_hi;         // M
+};
+
+__device__ __forceinline__ uint64_t shoup64(uint64_t b, uint64_t z, uint64_t zp, uint64_t m)
+{
+    return b * z - __umul64hi(b, zp) * m;           // in [0, 2m) for any b < 2^64
+}
+
+__device__ __forceinline__ uint64_t csub64(uint64_t v, uint64_t m) { return v >= m ? v - m : v; }
+
+// <x>_m for a signed 64-bit x: reduce its two's-complement bits, then take
+// away 2^64 mod m when x is negative.
+__device__ __forceinline__ uint64_t residue(long long x, const PrimeC &p)
+{
+    uint64_t r = csub64(shoup64((uint64_t)x, 1, p.onep, p.m), p.m);
+    if (x < 0) r = r >= p.r64 ? r - p.r64 : r + p.m - p.r64;
+    return r;
+}
+
+__global__ void k_exact_residues(const __grid_constant__ ExactArgs a, const long long *__restrict__ x, void *const *out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const long long v = x[i];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j >= a.k) break;
+            const uint64_t r = residue(v, a.p[j]);
+            if (a.p[j].word == 32) static_cast<uint32_t *>(out[j])[i] = (uint32_t)r;
+            else static_cast<uint64_t *>(out[j])[i] = r;
+        }
+    }
+}
+
+__global__ void k_exact_garner(const __grid_constant__ ExactArgs a, void *const *res, long long *__restrict__ h)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const u128 half = ((u128)a.half_hi << 64) | a.half_lo;
+    const u128 M = ((u128)a.M_hi << 64) | a.M_lo;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        uint64_t v[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j >= a.k) break;
+            const PrimeC &pj = a.p[j];
+            uint64_t t = pj.word == 32 ? (uint64_t) static_cast<const uint32_t *>(res[j])[i]
+                                       : static_cast<const uint64_t *>(res[j])[i];
+            // mixed-radix digit: t = (...((r_j - v_0) c_0j - v_1) c_1j ...) mod m_j
+#pragma unroll
+            for (int q = 0; q < KMAX; ++q) {
+                if (q >= j) break;
+                const uint64_t vq = csub64(shoup64(v[q], 1, pj.onep, pj.m), pj.m);     // v_q mod m_j
+                const uint64_t d = t >= vq ? t - vq : t + pj.m - vq;
+                t = csub64(shoup64(d, a.inv[q][j], a.invp[q][j], pj.m), pj.m);
+            }
+            v[j] = t;
+        }
+        // X = v_0 + m_0 (v_1 + m_1 (v_2 + ...)), Horner from the top digit
+        u128 X = 0;
+#pragma unroll
+        for (int j = KMAX - 1; j >= 0; --j)
+            if (j < a.k) X = X * a.p[j].m + v[j];
+        const i128 s = X > half ? (i128)X - (i128)M : (i128)X;
+        h[i] = (long long)s;
+    }
+}
+
+// Candidate primes: prime factors of Fermat numbers with ord_p(2) = 2^(n+1)
+// for p | F_n (Sec. III-A, Prop. 2).  Each is re-validated by ntt_plan
+// (primality, order a power of two, N | order) before use.  32-bit-word
+// primes (below 2^25) come first: they run the faster path.
+const uint64_t kCandidates[] = {
+    13631489ull,      // F_18, Table 1
+    26017793ull,      // F_12
+    6700417ull,       // F_5
+    2424833ull,       // F_9, Table 1
+    974849ull,        // F_11
+    319489ull,        // F_11, Table 1
+    274177ull,        // F_6
+    114689ull,        // F_12
+    641ull,           // F_5, Table 1
+    70525124609ull,   // F_19 (64-bit words)
+    167772161ull,     // F_23
+    1214251009ull,    // F_15
+    825753601ull,     // F_16
+    63766529ull,      // F_12
+    45592577ull,      // F_10
+};
+
+}  // namespace
+
+struct ntt_exact_s {
+    uint32_t N = 0;
+    uint32_t bound_bits = 0;
+    int k = 0;
+    ntt_plan_t plans[KMAX] = {};
+    ExactArgs args{};
+    double capacity_bits = 0;
+    size_t wave = 0;                  // pairs per scratch wave
+    void *scratch = nullptr;          // per prime: F (reused for H) and G residues of one wave
+    void **ptrs_f = nullptr;          // device arrays of KMAX pointers
+    void **ptrs_g = nullptr;
+    void *host_ptrs[2 * KMAX] = {};   // the same pointers, host side
+    int nsm = 0;
+};
+
+extern "C" void ntt_exact_destroy(ntt_exact_t e)
+{
+    if (!e) return;
+    for (int i = 0; i < e->k; ++i) ntt_plan_destroy(e->plans[i]);
+    cudaFree(e->scratch);
+    cudaFree(e->ptrs_f);
+    cudaFree(e->ptrs_g);
+    delete e;
+}
+
+extern "C" ntt_status ntt_exact_plan(uint32_t N, uint32_t bound_bits, ntt_exact_t *out)
+{
+    if (!out) return ntt_fail(NTT_ERR_ARG, "ntt_exact_plan: NULL out");
+    *out = nullptr;
+    if (N == 0 || (N & (N - 1))) return ntt_fail(NTT_ERR_LENGTH, "ntt_exact_plan: N=%u is not a power of two", N);
+    if (bound_bits == 0 || bound_bits > 63)
+        return ntt_fail(NTT_ERR_RANGE, "ntt_exact_plan: bound_bits=%u outside 1..63 (outputs are signed 64-bit)", bound_bits);
+    ntt_exact_s *e = new ntt_exact_s();
+    e->N = N;
+    e->bound_bits = bound_bits;
+    auto bail = [&](ntt_status s) { ntt_exact_destroy(e); return s; };
+    // Greedy: candidates in order until M = prod m_i >= 2^(bound + 1), which
+    // makes every h in (-2^bound, 2^bound) a distinct residue class and the
+    // signed representative in (-M/2, M/2] equal to h.  M stays below 2^101.
+    const u128 need = (u128)1 << (bound_bits + 1);
+    u128 prod = 1;
+    double bits = 0;
+    for (uint64_t m : kCandidates) {
+        if (e->k == KMAX || prod >= need) break;
+        ntt_plan_t p = nullptr;
+        if (ntt_plan(m, N, &p) != NTT_OK) continue;      // N does not divide ord_m(2), or above the supported length
+        e->plans[e->k++] = p;
+        prod *= m;
+        bits += std::log2((double)m);
+    }
+    if (prod < need)
+        return bail(ntt_fail(NTT_ERR_LENGTH, "ntt_exact_plan: the Rader primes available for N=%u give %.1f bits, %u + 1 needed",
+                             N, bits, bound_bits));
+    e->capacity_bits = bits;
+    // constants
+    ExactArgs &a = e->args;
+    a.k = e->k;
+    u128 M = 1;
+    for (int i = 0; i < e->k; ++i) {
+        ntt_plan_info_t info;
+        ntt_plan_get_info(e->plans[i], &info);
+        const uint64_t m = info.m;
+        a.p[i].m = m;
+        a.p[i].onep = (uint64_t)(((u128)1 << 64) / m);
+        a.p[i].r64 = (uint64_t)(((u128)1 << 64) % m);
+        a.p[i].word = (int)info.word_bits;
+        M *= m;
+    }
+    for (int i = 0; i < e->k; ++i)
+        for (int j = i + 1; j < e->k; ++j) {
+            const uint64_t mj = a.p[j].m;
+            const uint64_t c = nt::pow_mod(a.p[i].m % mj, mj - 2, mj);     // m_i^-1 mod m_j (m_j prime)
+            a.inv[i][j] = c;
+            a.invp[i][j] = (uint64_t)(((u128)c << 64) / mj);
+        }
+    const u128 half = (M - 1) / 2;
+    a.half_lo = (unsigned long long)half;
+    a.half_hi = (unsigned long long)(half >> 64);
+    a.M_lo = (unsigned long long)M;
+    a.M_hi = (unsigned long long)(M >> 64);
+    // scratch: waves of pairs, at most 256 MiB of residues
+    size_t per_pair = 0;
+    for (int i = 0; i < e->k; ++i) per_pair += 2 * (size_t)N * (a.p[i].word / 8);
+    e->wave = std::min<size_t>(65536, std::max<size_t>(1, ((size_t)256 << 20) / per_pair));
+    if (cudaMalloc(&e->scratch, e->wave * per_pair) != cudaSuccess ||
+        cudaMalloc((void **)&e->ptrs_f, 2 * KMAX * sizeof(void *)) != cudaSuccess)
+        return bail(ntt_fail(NTT_ERR_OOM, "ntt_exact_plan: scratch"));
+    e->ptrs_g = e->ptrs_f + KMAX;
+    void *host[2 * KMAX] = {};
+    unsigned char *base = (unsigned char *)e->scratch;
+    for (int i = 0; i < e->k; ++i) {
+        const size_t bytes = e->wave * (size_t)N * (a.p[i].word / 8);
+        host[i] = base;
+        host[KMAX + i] = base + bytes;
+        base += 2 * bytes;
+    }
+    if (cudaMemcpy(e->ptrs_f, host, sizeof host, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(ntt_fail(NTT_ERR_CUDA, "ntt_exact_plan: upload"));
+    memcpy(e->host_ptrs, host, sizeof host);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
+    *out = e;
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_exact_get_info(ntt_exact_t e, ntt_exact_info_t *info)
+{
+    if (!e || !info) return ntt_fail(NTT_ERR_ARG, "ntt_exact_get_info: NULL argument");
+    memset(info, 0, sizeof *info);
+    info->N = e->N;
+    info->bound_bits = e->bound_bits;
+    info->nprimes = (uint32_t)e->k;
+    for (int i = 0; i < e->k; ++i) {
+        info->primes[i] = e->args.p[i].m;
+        info->word_bits[i] = (uint32_t)e->args.p[i].word;
+    }
+    info->capacity_bits = e->capacity_bits;
+    info->wave = (uint64_t)e->wave;
+    return NTT_OK;
+}
+
+extern "C" ntt_status conv_exact(ntt_exact_t e, const int64_t *f, const int64_t *g, int64_t *h, size_t batch,
+                                 ntt_stream_t stream)
+{
+    if (!e || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_exact: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int threads = 256;
+    for (size_t p0 = 0; p0 < batch; p0 += e->wave) {
+        const size_t np = std::min(e->wave, batch - p0);
+        ExactArgs a = e->args;
+        a.n = (long long)(np * e->N);
+        const int grid = (int)std::min<long long>((a.n + threads - 1) / threads, (long long)e->nsm * 8);
+        const size_t off = p0 * e->N;
+        k_exact_residues<<<grid, threads, 0, st>>>(a, (const long long *)f + off, e->ptrs_f);
+        k_exact_residues<<<grid, threads, 0, st>>>(a, (const long long *)g + off, e->ptrs_g);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: residues: %s", cudaGetErrorString(err));
+        for (int i = 0; i < e->k; ++i) {
+            ntt_status s = conv_circular(e->plans[i], e->host_ptrs[i], e->host_ptrs[KMAX + i], e->host_ptrs[i], np, stream);
+            if (s != NTT_OK) return s;
+        }
+        k_exact_garner<<<grid, threads, 0, st>>>(a, e->ptrs_f, (long long *)h + off);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: reconstruction: %s", cudaGetErrorString(err));
+    }
+    return NTT_OK;
+}

@@ -52,6 +52,10 @@ SIGNATURES = {
     "ntt_server_get_stats": (_INT, [_VP, _VP]),
     "ntt_server_reset_stats": (_INT, [_VP]),
     "ntt_server_destroy": (None, [_VP]),
+    "ntt_exact_plan": (_INT, [_U32, _U32, ctypes.POINTER(_VP)]),
+    "ntt_exact_get_info": (_INT, [_VP, _VP]),
+    "conv_exact": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
+    "ntt_exact_destroy": (None, [_VP]),
 }
 
 
@@ -66,6 +70,16 @@ class PlanInfo(ctypes.Structure):
                 ("n_max", ctypes.c_uint64), ("omega", ctypes.c_uint64), ("n_inv", ctypes.c_uint64),
                 ("word_bits", ctypes.c_uint32), ("four_step", ctypes.c_uint32), ("wave", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+EXACT_MAX_PRIMES = 4
+
+
+class ExactInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("bound_bits", ctypes.c_uint32), ("nprimes", ctypes.c_uint32),
+                ("word_bits", ctypes.c_uint32 * EXACT_MAX_PRIMES), ("reserved", ctypes.c_uint32),
+                ("primes", ctypes.c_uint64 * EXACT_MAX_PRIMES), ("capacity_bits", ctypes.c_double),
+                ("wave", ctypes.c_uint64)]
 
 
 class ConvDesc(ctypes.Structure):
@@ -214,6 +228,55 @@ def conv_circular_noalloc(plan: Plan, f: torch.Tensor, g: torch.Tensor, out: tor
         raise ValueError("f, g and out must hold the same number of sequences")
     _check(lib().conv_circular_noalloc(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b,
                                        _stream(stream)), "conv_circular_noalloc")
+    return out
+
+
+class ExactPlan:
+    """``ntt_exact_plan(N, bound_bits)``: exact integer convolutions of length
+    N whose outputs satisfy |h| < 2^bound_bits, by the Chinese remainder
+    theorem over Rader primes."""
+
+    def __init__(self, N: int, bound_bits: int):
+        h = ctypes.c_void_p()
+        _check(lib().ntt_exact_plan(N, bound_bits, ctypes.byref(h)), f"ntt_exact_plan(N={N}, bound_bits={bound_bits})")
+        self.handle = h
+        info = ExactInfo()
+        _check(lib().ntt_exact_get_info(h, ctypes.byref(info)), "ntt_exact_get_info")
+        self.N = int(info.N)
+        self.bound_bits = int(info.bound_bits)
+        self.primes = [int(info.primes[i]) for i in range(info.nprimes)]
+        self.word_bits = [int(info.word_bits[i]) for i in range(info.nprimes)]
+        self.capacity_bits = float(info.capacity_bits)
+        self.wave = int(info.wave)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().ntt_exact_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def conv_exact(plan: ExactPlan, f: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """Exact circular convolution of int64 sequences ([batch][N] or [N])."""
+    for t, name in ((f, "f"), (g, "g")):
+        if t.dtype != torch.int64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous int64 CUDA tensor")
+        if t.shape[-1] != plan.N:
+            raise ValueError(f"{name} has length {t.shape[-1]}, the plan N={plan.N}")
+    if f.shape != g.shape:
+        raise ValueError("f and g must have the same shape")
+    out = torch.empty_like(f) if out is None else out
+    if out.shape != f.shape or out.dtype != torch.int64 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int64 tensor shaped like f")
+    b = f.numel() // plan.N
+    _check(lib().conv_exact(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, _stream(stream)),
+           "conv_exact")
     return out
 
 

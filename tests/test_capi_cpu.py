@@ -80,3 +80,33 @@ def test_torch_generator_matches_numpy():
         a = inputs.uniform_mod(m, 5000, seed=11, stream=3, start=777, dtype=np.uint64)
         b = inputs.uniform_mod_torch(m, 5000, seed=11, stream=3, start=777, device="cpu", dtype=torch.int64)
         assert np.array_equal(a, b.numpy().astype(np.uint64))
+
+
+@pytest.mark.parametrize("N,bits,status", [
+    (3, 20, 1),             # not a power of two
+    (0, 20, 1),
+    (1024, 0, 4),           # bound outside 1..63: outputs are signed 64-bit
+    (1024, 64, 4),
+])
+def test_exact_plan_rejects(ntt, N, bits, status):
+    h = ctypes.c_void_p()
+    assert ntt.lib().ntt_exact_plan(N, bits, ctypes.byref(h)) == status
+    assert not h.value
+    assert ntt.lib().ntt_exact_plan(1024, 20, None) == 8
+    assert ntt.lib().conv_exact(None, None, None, None, 1, None) == 8
+
+
+def test_exact_candidate_primes_are_fermat_factors(orc):
+    """Every prime the exact convolution may use is a prime factor of the
+    Fermat number its table entry names, so ord_p(2) = 2^(n+1) (Sec. III-A)."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1005_1497_gb300", "csrc", "ntt_exact.cu")).read()
+    table = src[src.index("kCandidates[]"):]
+    table = table[:table.index("};")]
+    rows = re.findall(r"(\d+)ull,\s*//\s*F_(\d+)", table)
+    assert len(rows) >= 10
+    for p, n in rows:
+        p, n = int(p), int(n)
+        assert orc.is_prime(p), p
+        assert pow(2, 1 << n, p) == p - 1, (p, n)          # p | F_n = 2^(2^n) + 1
+        assert orc.order(2, p) == 1 << (n + 1), (p, n)
