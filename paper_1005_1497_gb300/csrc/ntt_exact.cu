@@ -146,8 +146,8 @@ struct ntt_exact_s {
     double capacity_bits = 0;
     size_t wave = 0;                  // pairs per scratch wave
     void *scratch = nullptr;          // per prime: F (reused for H) and G residues of one wave
-    void **ptrs_f = nullptr;          // device arrays of KMAX pointers
-    void **ptrs_g = nullptr;
+    void **ptrs_f = nullptr;          // device array of 2 KMAX pointers: F residues, then G
+    void **ptrs_g = nullptr;          // ptrs_f + KMAX
     void *host_ptrs[2 * KMAX] = {};   // the same pointers, host side
     int nsm = 0;
 };
@@ -157,8 +157,7 @@ extern "C" void ntt_exact_destroy(ntt_exact_t e)
     if (!e) return;
     for (int i = 0; i < e->k; ++i) ntt_plan_destroy(e->plans[i]);
     cudaFree(e->scratch);
-    cudaFree(e->ptrs_f);
-    cudaFree(e->ptrs_g);
+    cudaFree(e->ptrs_f);             // ptrs_g points into the same allocation
     delete e;
 }
 
