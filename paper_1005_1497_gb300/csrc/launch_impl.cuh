@@ -97,7 +97,7 @@ template <typename W, int L>
 static cudaError_t launch_conv_split(const RowArgs<W> &a, int grid, cudaStream_t st)
 {
     constexpr int LR = LRMax<W>::v;
-    if constexpr (L > LR && L <= LR + 5) {
+    if constexpr (L > LR && L <= Launch<W>::LMAX) {
         constexpr size_t smem = CRShape<W, L, LR>::smem;
         static const cudaError_t init = ensure_smem(k_conv_cr<W, L, LR, 0>, smem);
         if (init != cudaSuccess) return init;
@@ -112,7 +112,7 @@ template <typename W, int L>
 static cudaError_t launch_rows_fwd(const RowArgs<W> &a, int grid, cudaStream_t st)
 {
     constexpr int LR = LRMax<W>::v;
-    if constexpr (L > LR && L <= LR + 5) {
+    if constexpr (L > LR && L <= Launch<W>::LMAX) {
         constexpr size_t smem = RowShape<W, L, LR>::smem(1);
         static const cudaError_t init = ensure_smem(k_rows_fwd<W, L, LR>, smem);
         if (init != cudaSuccess) return init;
@@ -123,14 +123,28 @@ static cudaError_t launch_rows_fwd(const RowArgs<W> &a, int grid, cudaStream_t s
     }
 }
 
+// Column bits of the split path: up to CMAX in one pass; above that, a top
+// pass of L - LR - LB bits and a middle pass of LB = (L - LR) / 2 bits.
+constexpr int CMAX = 5;
+template <typename W, int L> struct ColSplit {
+    static constexpr int LR = LRMax<W>::v;
+    static constexpr int LC = L - LR;
+    static constexpr bool TWO = LC > CMAX;
+    static constexpr int LB = TWO ? LC / 2 : 0;          // middle bits
+    static constexpr int TOPLR = LR + LB;                // "row" bits seen by the top pass
+};
+
 template <typename W, int L, int NS, int SRC>
 static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
 {
-    constexpr int LR = LRMax<W>::v;
-    if constexpr (L > LR && L <= LR + 5) {
-        const long long threads = a.npairs << LR;
-        const int blocks = (int)((threads + 255) / 256);
-        k_cols_fwd<W, L, LR, NS, SRC><<<blocks, 256, 0, st>>>(a);
+    using CS = ColSplit<W, L>;
+    if constexpr (L > CS::LR && L <= Launch<W>::LMAX) {
+        const long long threads = a.npairs << CS::TOPLR;
+        k_cols_fwd<W, L, CS::TOPLR, NS, SRC><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
+        if constexpr (CS::TWO) {
+            const long long t2 = a.npairs << (L - CS::LB);
+            k_cols_mid_fwd<W, L, CS::LR, CS::LB, NS><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
+        }
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
@@ -140,11 +154,14 @@ static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
 template <typename W, int L, int DST>
 static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
 {
-    constexpr int LR = LRMax<W>::v;
-    if constexpr (L > LR && L <= LR + 5) {
-        const long long threads = a.npairs << LR;
-        const int blocks = (int)((threads + 255) / 256);
-        k_cols_inv<W, L, LR, DST><<<blocks, 256, 0, st>>>(a);
+    using CS = ColSplit<W, L>;
+    if constexpr (L > CS::LR && L <= Launch<W>::LMAX) {
+        if constexpr (CS::TWO) {
+            const long long t2 = a.npairs << (L - CS::LB);
+            k_cols_mid_inv<W, L, CS::LR, CS::LB><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
+        }
+        const long long threads = a.npairs << CS::TOPLR;
+        k_cols_inv<W, L, CS::TOPLR, DST><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
@@ -185,7 +202,7 @@ static cudaError_t launch_bitrev(const W *src, W *dst, long long batch, const Mo
     case 9: return CALL(9); case 10: return CALL(10); case 11: return CALL(11);          \
     case 12: return CALL(12); case 13: return CALL(13); case 14: return CALL(14);        \
     case 15: return CALL(15); case 16: return CALL(16); case 17: return CALL(17);        \
-    case 18: return CALL(18); case 19: return CALL(19);                                  \
+    case 18: return CALL(18); case 19: return CALL(19); case 20: return CALL(20);        \
     default: return cudaErrorInvalidValue;                                               \
     }
 

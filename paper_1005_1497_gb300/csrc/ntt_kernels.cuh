@@ -687,6 +687,56 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
     }
 }
 
+// Split path with more column bits than one thread holds (L - LR > 5):
+// the top bits run in k_cols_fwd / k_cols_inv with LR' = BLO + LB, and the
+// middle bits [BLO, BLO + LB) in these kernels, in place in the wave's
+// scratch.  Element x = lo + (k << BLO) + (hi << (BLO + LB)); the node of
+// register bit J is x >> (BLO + J + 1) = (hi << (LB - J - 1)) | (k >> (J + 1)),
+// so a column's twiddles depend on its top bits hi (read from the plan's
+// table).  Forward: after the top bits; inverse (transposed): before them.
+template <typename W, int L, int BLO, int LB, int NS>
+__global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ ColArgs<W> a)
+{
+    constexpr int RC = 1 << LB, LO = L - LB;           // LO: bits outside the register group
+    constexpr uint32_t N = 1u << L;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.npairs << LO) return;
+    const long long pw = idx >> LO;
+    const uint32_t r = (uint32_t)idx & ((1u << LO) - 1u);
+    const uint32_t lo = r & ((1u << BLO) - 1u), hi = r >> BLO;
+    const uint32_t base = lo + (hi << (BLO + LB));
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        W *p = (s == 0 ? a.dst0 : a.dst1) + (size_t)pw * N;
+        W v[RC];
+#pragma unroll
+        for (int k = 0; k < RC; ++k) v[k] = p[base + ((uint32_t)k << BLO)];
+        colf_levels<W, LB, 0, LB - 1, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
+#pragma unroll
+        for (int k = 0; k < RC; ++k) p[base + ((uint32_t)k << BLO)] = v[k];
+    }
+}
+
+template <typename W, int L, int BLO, int LB>
+__global__ void __launch_bounds__(256) k_cols_mid_inv(const __grid_constant__ ColArgs<W> a)
+{
+    constexpr int RC = 1 << LB, LO = L - LB;
+    constexpr uint32_t N = 1u << L;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.npairs << LO) return;
+    const long long pw = idx >> LO;
+    const uint32_t r = (uint32_t)idx & ((1u << LO) - 1u);
+    const uint32_t lo = r & ((1u << BLO) - 1u), hi = r >> BLO;
+    const uint32_t base = lo + (hi << (BLO + LB));
+    W *p = a.dst0 + (size_t)pw * N;
+    W v[RC];
+#pragma unroll
+    for (int k = 0; k < RC; ++k) v[k] = p[base + ((uint32_t)k << BLO)];
+    colg_levels<W, LB, 0, 0, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
+#pragma unroll
+    for (int k = 0; k < RC; ++k) p[base + ((uint32_t)k << BLO)] = v[k];
+}
+
 // Forward row levels of the split path (single sequence, in place in scratch).
 template <typename W, int L, int LR>
 __global__ void __launch_bounds__(BLOCK, 1) k_rows_fwd(const __grid_constant__ RowArgs<W> a)

@@ -9,14 +9,15 @@ namespace ntt {
 
 template <typename W> struct Launch {
     static constexpr int LRMAX = LRMax<W>::v;
-    static constexpr int LMAX = LRMAX + 5;     // split path: up to 5 column bits
+    static constexpr int LMAX = 20;            // split path: LMAX - LRMAX column bits, in two passes above 5
     // rows transformed concurrently by one block of the row kernels
     static int rows_per_block(int LR);
     // pairs in flight per block of the whole-sequence fused kernels
     static int pairs_per_block(int L);
     // whole-sequence fused convolution (L <= LRMAX); src 0 = contiguous, 1 = descriptors
     static cudaError_t conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st);
-    // split path pieces (LRMAX < L <= LMAX)
+    // split path pieces (LRMAX < L <= LMAX); cols_fwd / cols_inv run one or
+    // two column passes
     static cudaError_t conv_rows_split(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
     static cudaError_t cols_fwd(int L, int ns, int src, const ColArgs<W> &a, cudaStream_t st);
     static cudaError_t cols_inv(int L, int dst, const ColArgs<W> &a, cudaStream_t st);

@@ -2,6 +2,8 @@
 Chinese remainder theorem over Rader primes) with the oracle's exact
 convolution in 128-bit integers: every output bit-exact, signed inputs up to
 the plan's bound, several primes, one-block and split lengths."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -39,14 +41,14 @@ def signed_inputs(batch, N, amp, seed):
 
 def amp_for(N, bound_bits):
     """Largest amplitude with N * amp^2 < 2^bound_bits."""
-    return int(np.floor(np.sqrt(((1 << bound_bits) - 1) / N)))
+    return math.isqrt(((1 << bound_bits) - 1) // N)
 
 
 CASES = [
     (1, 20, 3), (2, 20, 3), (8, 40, 5), (64, 30, 7), (64, 62, 3),
     (1024, 31, 5), (1024, 47, 4), (1024, 63, 3),
     (4096, 44, 3), (1 << 14, 46, 2), (1 << 15, 40, 2), (1 << 17, 50, 2), (1 << 18, 58, 2),
-    (1 << 19, 22, 2),
+    (1 << 19, 22, 2), (1 << 19, 58, 2), (1 << 20, 62, 2),
 ]
 
 
@@ -84,6 +86,9 @@ def test_conv_exact_prime_choice(ntt):
     assert all(w == 32 for w in wide.word_bits) and len(wide.primes) == 3
     big = ntt.ExactPlan(1 << 19, 22)
     assert big.primes == [13631489]
+    longest = ntt.ExactPlan(1 << 20, 62)          # only the 64-bit-word primes admit 2^20
+    assert longest.primes == [70525124609, 167772161] and longest.word_bits == [64, 64]
+    longest.close()
     for p in (small, wide, big):
         p.close()
 

@@ -82,7 +82,7 @@ def test_conv_u32_split(ntt, orc, L):
         assert np.array_equal(h[b][idx.astype(np.int64)], orc.conv_sample(f[b], g[b], M, idx))
 
 
-@pytest.mark.parametrize("L", [0, 1, 3, 4, 5, 8, 12, 13, 14, 15, 16, 18])
+@pytest.mark.parametrize("L", [0, 1, 3, 4, 5, 8, 12, 13, 14, 15, 16, 18, 19, 20])
 def test_conv_u64(ntt, orc, L):
     N = 1 << L
     plan = ntt.Plan(M64, N)
@@ -95,7 +95,7 @@ def test_conv_u64(ntt, orc, L):
 
 
 @pytest.mark.parametrize("m,L", [(641, 6), (2424833, 10), (M, 1), (M, 7), (M, 11), (M, 14), (M, 15), (M, 19),
-                                 (M64, 9), (M64, 14)])
+                                 (M64, 9), (M64, 14), (M64, 19), (M64, 20)])
 def test_ntt_forward_inverse(ntt, orc, m, L):
     N = 1 << L
     plan = ntt.Plan(m, N)
@@ -122,12 +122,12 @@ def test_conv_plain_form(ntt, orc, m, L):
 
 
 @pytest.mark.parametrize("m", [M, M64])
-@pytest.mark.parametrize("L", [1, 6, 10, 14, 17])
+@pytest.mark.parametrize("L", [1, 6, 10, 14, 17, 19, 20])
 def test_extreme_inputs(ntt, orc, m, L):
     """All words m-1 (the lazy bounds' worst case): h(j) = N (m-1)^2 = N mod m."""
     N = 1 << L
-    if m == M64 and L > 18:
-        pytest.skip()
+    if m == M and L > 19:
+        pytest.skip("2^20 does not divide ord_m(2) = 2^19")
     plan = ntt.Plan(m, N)
     wb = plan.word_bits
     f = np.full((2, N), m - 1, dtype=np.uint64)
