@@ -8,7 +8,7 @@ m = 13631489, 32-bit words (the uniform-batch configuration).  Prints ONE
 JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload conv2|conv1|conv3|conv4|serve5|exact6] [--quick]
+                    [--workload conv2|conv1|conv3|conv4|serve5|exact6|shift7] [--quick]
 
 Multi-GPU (torchrun): every rank convolves its own batch (independent pairs,
 no collective on the data path); the timing is the max over ranks and the
@@ -39,6 +39,8 @@ WORKLOADS = {
                            "{8..18}, m=70525124609 (factor of F_19), uint64, continuous batching, pool-admitted"),
     "conv4": (10000, None, "uneven batch: 10000 pairs, N = 2^k with k uniform on {6..19}, m=13631489, uint32, "
                            "one batch plan replayed as a CUDA graph"),
+    "shift7": (1 << 21, 6, "strict bit-shift transform: 2^21 pairs x N=64, m=641 (a factor of F_5), twiddles "
+                           "as shifts modulo F_5, against the same kernel with Shoup products and the main path"),
     "exact6": (8192, 12, "exact integer filtering: 8192 pairs x N=2^12 of signed 16-bit samples and taps "
                          "(|h| <= 2^42), int64 in and out, Chinese remainder theorem over Rader primes"),
 }
@@ -243,6 +245,8 @@ def run_ours(args):
         return run_serve(args, world, rank, local)
     if args.workload == "exact6":
         return run_exact(args, world, rank, local)
+    if args.workload == "shift7":
+        return run_shift(args, world, rank, local)
     batch, L, desc = WORKLOADS[args.workload]
     N = 1 << L
     tuned = ntt.ntt_autotune(M, N, batch) if L > 14 else None     # split path: pick pairs per wave
@@ -361,6 +365,67 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_shift(args, world, rank, local):
+    """The strict bit-shift form (twiddles 2^e, e < 32, applied modulo F_5 =
+    2^32 + 1 by shift and lo - hi; m = 641 divides F_5) against the same
+    kernel with Shoup products modulo m and against the main fused path."""
+    import numpy as np
+    import torch
+
+    from paper_1005_1497_gb300 import inputs, ntt
+
+    batch, L, desc = WORKLOADS["shift7"]
+    N, m = 1 << L, 641
+    seed = 1000 + rank
+    f = inputs.uniform_mod_torch(m, batch * N, seed, 0, device="cuda").view(batch, N)
+    g = inputs.uniform_mod_torch(m, batch * N, seed, 1, device="cuda").view(batch, N)
+    h = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+    plan = ntt.Plan(m, N)
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(world, e0.elapsed_time(e1) / steps)
+
+    steps = max(1, min(args.steps, 500))
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: ntt.conv_circular_shift(m, f, g, out=h, mode=ntt.SHIFT_STRICT, stream=stream), steps)
+    ref = h.clone()
+    ms_shoup = timed(lambda: ntt.conv_circular_shift(m, f, g, out=h, mode=ntt.SHIFT_SHOUP, stream=stream), steps)
+    same_shoup = bool(torch.equal(h, ref))
+    ms_main = timed(lambda: ntt.conv_circular(plan, f, g, out=h, stream=stream), steps)
+    same_main = bool(torch.equal(h, ref))
+    hbm_peak, sm_max_mhz, peak_src = peaks()
+    alg_bytes = 12.0 * N * batch
+    hbm_ach = alg_bytes / (ms * 1e-3) / 1e9
+    rate = lambda t: round(batch * world * 1000.0 / t, 1)
+    out = {"metric": METRIC, "value": rate(ms), "unit": "conv/s", "n_gpus": world, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64 lanes modulo F_5 (u32 in and out)",
+           "data": "synthetic (seeded counter-based uniform residues in [0,641))",
+           "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "m": m,
+                      "l2": "inputs larger than L2 (1 GiB of f+g); no flush"},
+           "roofline": {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(hbm_ach / hbm_peak, 4), "traffic": None, "peak_src": f"{peak_src} copy bandwidth",
+                        "kernel": "k_conv_shift<32, 6, strict>", "algorithmic_bytes_per_step": alg_bytes},
+           "compare": {"same_kernel_shoup_products": {"value": rate(ms_shoup), "ms_per_step": round(ms_shoup, 4),
+                                                      "bit_identical": same_shoup},
+                       "main_fused_path": {"value": rate(ms_main), "ms_per_step": round(ms_main, 4),
+                                           "bit_identical": same_main}},
+           "clocks": clk.summary(), "gpu_launches": steps}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def run_exact(args, world, rank, local):

@@ -343,6 +343,29 @@ ntt_status conv_exact(ntt_exact_t plan, const int64_t *f_dev, const int64_t *g_d
 /* Release the plan, its modular plans and its scratch.  NULL is a no-op. */
 void ntt_exact_destroy(ntt_exact_t plan);
 
+/* ------------------------------------------------- strict bit-shift form */
+
+/* Circular convolution modulo a Rader prime m that divides F_4 = 2^16 + 1
+ * (m = 65537, N <= 32) or F_5 = 2^32 + 1 (m = 641 or 6700417, N <= 64):
+ * the regime where the transform of Eq. 2 / Eq. 3 is literally "bit-shifts,
+ * additions and modulo" (Sec. I; Sec. III-A, Prop. 2), because every
+ * twiddle 2^e has e < 2^t.
+ *   mode NTT_SHIFT_STRICT: the transform runs modulo F_t; each twiddle is a
+ *     shift followed by the multiply-free reduction lo - hi (2^(2^t) = -1),
+ *     N^-1 is a shift; only the N pointwise products multiply; the result is
+ *     reduced modulo m at the end.
+ *   mode NTT_SHIFT_SHOUP: the same kernel with every twiddle applied as a
+ *     Shoup product modulo m (the multiply form), for comparison.
+ * f_dev, g_dev: uint32 residues in [0, m), row-major [batch][N]; h_dev:
+ * uint32, canonical; device memory owned by the caller; h may not alias f
+ * or g.  Identical results in both modes (and to conv_circular).
+ * Errors: NTT_ERR_ARG, NTT_ERR_MODULUS (m not a prime factor of F_4 or F_5),
+ * NTT_ERR_LENGTH (N not a power of two in 2..ord_m(2)), NTT_ERR_CUDA. */
+#define NTT_SHIFT_STRICT 0
+#define NTT_SHIFT_SHOUP 1
+ntt_status conv_circular_shift(uint64_t m, uint32_t N, const uint32_t *f_dev, const uint32_t *g_dev, uint32_t *h_dev,
+                               size_t batch, int mode, ntt_stream_t stream);
+
 /* ----------------------------------------------------------------- checks */
 
 /* Count the words of `count` words at data_dev (word size of the plan) that

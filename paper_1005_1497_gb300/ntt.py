@@ -56,6 +56,7 @@ SIGNATURES = {
     "ntt_exact_get_info": (_INT, [_VP, _VP]),
     "conv_exact": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
     "ntt_exact_destroy": (None, [_VP]),
+    "conv_circular_shift": (_INT, [_U64, _U32, _VP, _VP, _VP, _SZ, _INT, _VP]),
 }
 
 
@@ -277,6 +278,27 @@ def conv_exact(plan: ExactPlan, f: torch.Tensor, g: torch.Tensor, out: torch.Ten
     b = f.numel() // plan.N
     _check(lib().conv_exact(plan.handle, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, _stream(stream)),
            "conv_exact")
+    return out
+
+
+SHIFT_STRICT, SHIFT_SHOUP = 0, 1
+
+
+def conv_circular_shift(m: int, f: torch.Tensor, g: torch.Tensor, out: torch.Tensor | None = None,
+                        mode: int = SHIFT_STRICT, stream=None) -> torch.Tensor:
+    """Convolution modulo a prime factor of F_4 or F_5 by the strict
+    bit-shift transform (mode SHIFT_STRICT) or the same kernel with Shoup
+    products (SHIFT_SHOUP).  int32/uint32 tensors [batch][N] or [N]."""
+    for t, name in ((f, "f"), (g, "g")):
+        if t.dtype not in (torch.int32, torch.uint32) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 32-bit CUDA tensor")
+    if f.shape != g.shape:
+        raise ValueError("f and g must have the same shape")
+    out = torch.empty_like(f) if out is None else out
+    N = f.shape[-1]
+    b = f.numel() // N
+    _check(lib().conv_circular_shift(m, N, f.data_ptr(), g.data_ptr(), out.data_ptr(), b, mode, _stream(stream)),
+           "conv_circular_shift")
     return out
 
 

@@ -110,3 +110,16 @@ def test_exact_candidate_primes_are_fermat_factors(orc):
         assert orc.is_prime(p), p
         assert pow(2, 1 << n, p) == p - 1, (p, n)          # p | F_n = 2^(2^n) + 1
         assert orc.order(2, p) == 1 << (n + 1), (p, n)
+
+
+@pytest.mark.parametrize("m,N,mode,status", [
+    (13631489, 64, 0, 2),   # not a factor of F_4 or F_5
+    (4294967297, 64, 0, 2), # F_5 itself is composite
+    (641, 128, 0, 1),       # ord_641(2) = 64
+    (65537, 64, 0, 1),      # ord_65537(2) = 32
+    (641, 48, 0, 1),        # not a power of two
+    (641, 64, 2, 8),        # unknown mode
+])
+def test_shift_rejects(ntt, m, N, mode, status):
+    buf = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    assert ntt.lib().conv_circular_shift(m, N, buf, buf, buf, 1, mode, None) == status
