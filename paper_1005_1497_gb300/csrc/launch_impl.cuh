@@ -93,19 +93,18 @@ int Launch<W>::pairs_per_block(int L)
     return BLOCK / (32 << (L - RW));
 }
 
-template <typename W, int L>
-static cudaError_t launch_conv_split(const RowArgs<W> &a, int grid, cudaStream_t st)
+// Rows of a convolution's split path: after the twist of the column pass
+// they are whole length-2^LR convolutions (forward, pointwise, inverse) with
+// the uniform table, so one kernel serves every L; output lazy, natural order.
+template <typename W>
+static cudaError_t launch_conv_rows(const RowArgs<W> &a, int grid, cudaStream_t st)
 {
     constexpr int LR = LRMax<W>::v;
-    if constexpr (L > LR && L <= Launch<W>::LMAX) {
-        constexpr size_t smem = CRShape<W, L, LR>::smem;
-        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, LR, 0>, smem);
-        if (init != cudaSuccess) return init;
-        k_conv_cr<W, L, LR, 0><<<grid, BLOCK, smem, st>>>(a);
-        return cudaGetLastError();
-    } else {
-        return cudaErrorInvalidValue;
-    }
+    constexpr size_t smem = CRShape<W, LR, LR>::smem;
+    static const cudaError_t init = ensure_smem(k_conv_cr<W, LR, LR, 0, 1>, smem);
+    if (init != cudaSuccess) return init;
+    k_conv_cr<W, LR, LR, 0, 1><<<grid, BLOCK, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename W, int L>
@@ -140,7 +139,7 @@ static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
     using CS = ColSplit<W, L>;
     if constexpr (L > CS::LR && L <= Launch<W>::LMAX) {
         const long long threads = a.npairs << CS::TOPLR;
-        k_cols_fwd<W, L, CS::TOPLR, NS, SRC><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
+        k_cols_fwd<W, L, CS::TOPLR, NS, SRC, NS == 2 && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         if constexpr (CS::TWO) {
             const long long t2 = a.npairs << (L - CS::LB);
             k_cols_mid_fwd<W, L, CS::LR, CS::LB, NS><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
@@ -161,7 +160,7 @@ static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
             k_cols_mid_inv<W, L, CS::LR, CS::LB><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
         }
         const long long threads = a.npairs << CS::TOPLR;
-        k_cols_inv<W, L, CS::TOPLR, DST><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
+        k_cols_inv<W, L, CS::TOPLR, DST, !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
@@ -222,9 +221,8 @@ cudaError_t Launch<W>::conv_full(int L, int src, const RowArgs<W> &a, int grid, 
 template <typename W>
 cudaError_t Launch<W>::conv_rows_split(int L, const RowArgs<W> &a, int grid, cudaStream_t st)
 {
-#define C(X) launch_conv_split<W, X>(a, grid, st)
-    NTT_SWITCH_L(C)
-#undef C
+    if (L <= LRMAX || L > LMAX) return cudaErrorInvalidValue;
+    return launch_conv_rows<W>(a, grid, st);
 }
 
 template <typename W>

@@ -84,6 +84,7 @@ struct ntt_plan_s {
     int LR = 0;
     uint32_t wave = 0;                 // pairs per scratch wave (split path)
     void *scratch = nullptr;           // 2 * wave * N words
+    void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
     int nsm = 1;
     int device = 0;
     unsigned long long *counter = nullptr;
@@ -122,6 +123,7 @@ extern "C" void ntt_plan_destroy(ntt_plan_t p)
     if (!p) return;
     cudaFree(p->tw);
     cudaFree(p->scratch);
+    cudaFree(p->pw);
     cudaFree(p->counter);
     cudaFree(p->stage);
     for (int i = 0; i < 2; ++i) {
@@ -193,6 +195,22 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         if (wave < 1) wave = 1;
         p->wave = (uint32_t)wave;
         if (cudaMalloc(&p->scratch, 2 * wave * N * elt) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: scratch");
+        // powers w^e, e < N, for the twist between the column and row passes
+        // (w^e = 2^{e N_Max / N}, again from the doubling sequence)
+        std::vector<uint64_t> all = nt::powers_of_two_by_doubling((nmax / N) * (uint64_t)N, m);
+        std::vector<unsigned char> tab(2 * (size_t)N * elt);
+        for (size_t e = 0; e < N; ++e) {
+            const uint64_t z = all[e * (nmax / N)], zp = nt::shoup_quot(z, m, B);
+            if (word == 32) {
+                uint32_t a[2] = {(uint32_t)z, (uint32_t)zp};
+                memcpy(&tab[2 * e * elt], a, sizeof a);
+            } else {
+                uint64_t a[2] = {z, zp};
+                memcpy(&tab[2 * e * elt], a, sizeof a);
+            }
+        }
+        if (cudaMalloc(&p->pw, tab.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: power table");
+        CUDA_TRY(cudaMemcpy(p->pw, tab.data(), tab.size(), cudaMemcpyHostToDevice), "ntt_plan: upload powers");
     }
     *out = p.release();
     return NTT_OK;
@@ -239,7 +257,7 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     const long long N = p->N;
     for (long long w0 = 0; w0 < batch; w0 += wave) {
         const long long np = std::min<long long>(wave, batch - w0);
-        ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c};
+        ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c, (const W *)p->pw};
         cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);

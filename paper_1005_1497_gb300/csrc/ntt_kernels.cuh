@@ -296,7 +296,9 @@ struct CRShape {
 // row and are read from the plan's table, the inverse ones do not and are
 // read from shared memory.
 // Rows [base + row group, end) by steps of stride; end is a.nrows unless ITEM.
-template <typename W, int L, int LROW, int SRC, bool ITEM = false>
+// OUT 0: canonical at <-x>_N (a whole convolution); OUT 1: lazy residues in
+// natural order (a row of a convolution's split path, after the twist).
+template <typename W, int L, int LROW, int SRC, bool ITEM = false, int OUT = 0>
 __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long stride, long long end = 0)
 {
     using SH = CRShape<W, L, LROW>;
@@ -435,17 +437,17 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
-                if constexpr (FULL) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
+                if constexpr (FULL && OUT == 0) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
                 else hcur[x] = v[0][j * RC + k];
             }
     }
 }
 
-template <typename W, int L, int LROW, int SRC>
+template <typename W, int L, int LROW, int SRC, int OUT = 0>
 __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(const __grid_constant__ RowArgs<W> a)
 {
     constexpr int PPC = CRShape<W, L, LROW>::PPC;
-    conv_cr_body<W, L, LROW, SRC>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC);
+    conv_cr_body<W, L, LROW, SRC, false, OUT>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC);
 }
 
 // ---- one persistent launch for every whole-sequence length of a batch ----
@@ -584,7 +586,32 @@ template <typename W> struct ColArgs {
     long long pair0;    // first pair of the wave in the batch / descriptor list
     const W *tw;
     ModC<W> c;
+    const W *pw;        // convolutions: (w^e, Shoup quotient) pairs, e < N (the twist)
 };
+
+// The four-step twist of a convolution's split path.  After the column
+// levels, element (r, t) -- r the top L - LR index bits at their tree
+// position, t the low LR bits -- is multiplied by w^(brv(r) t).  That turns
+// every row's remaining levels into the length-2^LR transform with the
+// uniform table z'_i = w'^brv(i), w' = w^(2^(L-LR)), whose entries are the
+// first 2^(LR-1) of the plan's table; the rows then run the whole-sequence
+// kernel.  The inverse (the transposed tree) applies the same diagonal
+// between the rows and the transposed column levels.  Output in [0, 2m).
+template <typename W, int L>
+__device__ __forceinline__ W twist(W v, uint32_t rbrv, uint32_t t, const W *__restrict__ pw, const ModC<W> &c)
+{
+    const uint32_t e = (rbrv * t) & ((1u << L) - 1u);
+    const W z = __ldg(pw + 2 * (size_t)e), zp = __ldg(pw + 2 * (size_t)e + 1);
+    return shoup<W>(v, z, zp, c.m);
+}
+
+template <int BITS>
+__host__ __device__ constexpr uint32_t brv_c32(uint32_t k)
+{
+    uint32_t r = 0;
+    for (int i = 0; i < BITS; ++i) r |= ((k >> i) & 1u) << (BITS - 1 - i);
+    return r;
+}
 
 // Pairs 0 .. CNT-1 of the plan's table (the same for every column).
 template <typename W, int CNT>
@@ -631,7 +658,7 @@ __device__ __forceinline__ void col_fwd_levels(W (&v)[1 << (L - LR)], const W *_
     }
 }
 
-template <typename W, int L, int LR, int NS, int SRC>
+template <typename W, int L, int LR, int NS, int SRC, bool TWIST>
 __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int RC = 1 << (L - LR);
@@ -654,6 +681,11 @@ __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArg
 #pragma unroll
         for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
         col_fwd_levels<W, L, LR, L - LR - 1>(v, a.tw, a.c);
+        if constexpr (TWIST) {
+#pragma unroll
+            for (int k = 0; k < RC; ++k)
+                v[k] = csub<W>(twist<W, L>(v[k], brv_c32<L - LR>((uint32_t)k), col, a.pw, a.c), a.c.m);
+        }
 #pragma unroll
         for (int k = 0; k < RC; ++k) dst[col + ((uint32_t)k << LR)] = v[k];
     }
@@ -663,7 +695,7 @@ __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArg
 // x = c + k 2^LR): node twiddles k >> (J + 1), the same for every column.
 // Inputs < 2m; then the output stage: index <-x>_N, canonical residue.
 // DST 0: contiguous out; 1: descriptor h.
-template <typename W, int L, int LR, int DST>
+template <typename W, int L, int LR, int DST, bool TWIST>
 __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int LC = L - LR, RC = 1 << LC;
@@ -679,6 +711,10 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
     W v[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
+    if constexpr (TWIST) {
+#pragma unroll
+        for (int k = 0; k < RC; ++k) v[k] = twist<W, L>(v[k], brv_c32<LC>((uint32_t)k), col, a.pw, a.c);
+    }
     colg_levels<W, LC, 0, 0, 0, TW_GLOBAL, RC>(v, 0u, a.tw, a.c);
 #pragma unroll
     for (int k = 0; k < RC; ++k) {
@@ -712,6 +748,12 @@ __global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ Co
 #pragma unroll
         for (int k = 0; k < RC; ++k) v[k] = p[base + ((uint32_t)k << BLO)];
         colf_levels<W, LB, 0, LB - 1, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
+        if constexpr (NS == 2) {                      // convolutions: the twist (brv over all L - BLO top bits)
+            const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
+#pragma unroll
+            for (int k = 0; k < RC; ++k)
+                v[k] = csub<W>(twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a.pw, a.c), a.c.m);
+        }
 #pragma unroll
         for (int k = 0; k < RC; ++k) p[base + ((uint32_t)k << BLO)] = v[k];
     }
@@ -732,6 +774,12 @@ __global__ void __launch_bounds__(256) k_cols_mid_inv(const __grid_constant__ Co
     W v[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) v[k] = p[base + ((uint32_t)k << BLO)];
+    {
+        const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
+#pragma unroll
+        for (int k = 0; k < RC; ++k)
+            v[k] = twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a.pw, a.c);
+    }
     colg_levels<W, LB, 0, 0, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
 #pragma unroll
     for (int k = 0; k < RC; ++k) p[base + ((uint32_t)k << BLO)] = v[k];
