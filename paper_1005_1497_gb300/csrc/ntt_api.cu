@@ -85,6 +85,7 @@ struct ntt_plan_s {
     uint32_t wave = 0;                 // pairs per scratch wave (split path)
     void *scratch = nullptr;           // 2 * wave * N words
     void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
+    void *pwl = nullptr;               // split path: (w^(s l), quotient) at s 32 + l, s < 2^(L - LR), l < 32
     int nsm = 1;
     int device = 0;
     unsigned long long *counter = nullptr;
@@ -124,6 +125,7 @@ extern "C" void ntt_plan_destroy(ntt_plan_t p)
     cudaFree(p->tw);
     cudaFree(p->scratch);
     cudaFree(p->pw);
+    cudaFree(p->pwl);
     cudaFree(p->counter);
     cudaFree(p->stage);
     for (int i = 0; i < 2; ++i) {
@@ -211,6 +213,23 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         }
         if (cudaMalloc(&p->pw, tab.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: power table");
         CUDA_TRY(cudaMemcpy(p->pw, tab.data(), tab.size(), cudaMemcpyHostToDevice), "ntt_plan: upload powers");
+        const size_t ns = (size_t)1 << (L - p->LR);
+        std::vector<unsigned char> lt(2 * ns * 32 * elt);
+        for (size_t sidx = 0; sidx < ns; ++sidx)
+            for (size_t l = 0; l < 32; ++l) {
+                const uint64_t e = (sidx * l) % N;
+                const uint64_t z = all[e * (nmax / N)], zp = nt::shoup_quot(z, m, B);
+                const size_t i = sidx * 32 + l;
+                if (word == 32) {
+                    uint32_t a[2] = {(uint32_t)z, (uint32_t)zp};
+                    memcpy(&lt[2 * i * elt], a, sizeof a);
+                } else {
+                    uint64_t a[2] = {z, zp};
+                    memcpy(&lt[2 * i * elt], a, sizeof a);
+                }
+            }
+        if (cudaMalloc(&p->pwl, lt.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: lane power table");
+        CUDA_TRY(cudaMemcpy(p->pwl, lt.data(), lt.size(), cudaMemcpyHostToDevice), "ntt_plan: upload lane powers");
     }
     *out = p.release();
     return NTT_OK;
@@ -257,7 +276,8 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     const long long N = p->N;
     for (long long w0 = 0; w0 < batch; w0 += wave) {
         const long long np = std::min<long long>(wave, batch - w0);
-        ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c, (const W *)p->pw};
+        ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c, (const W *)p->pw,
+                      (const W *)p->pwl};
         cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);

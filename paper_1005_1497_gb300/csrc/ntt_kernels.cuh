@@ -587,6 +587,7 @@ template <typename W> struct ColArgs {
     const W *tw;
     ModC<W> c;
     const W *pw;        // convolutions: (w^e, Shoup quotient) pairs, e < N (the twist)
+    const W *pwl;       // (w^(s l), quotient) at s 32 + l, s < 2^(L-LR), l < 32
 };
 
 // The four-step twist of a convolution's split path.  After the column
@@ -597,12 +598,20 @@ template <typename W> struct ColArgs {
 // first 2^(LR-1) of the plan's table; the rows then run the whole-sequence
 // kernel.  The inverse (the transposed tree) applies the same diagonal
 // between the rows and the transposed column levels.  Output in [0, 2m).
+//
+// The factor is split as w^(s t0) w^(s l) with t = t0 + l, l = t mod 32 (the
+// lane): the first is the same for a warp (one broadcast load), the second
+// comes from a small lane-contiguous table (a coalesced load); two Shoup
+// products, in kernels bound by HBM.
 template <typename W, int L>
-__device__ __forceinline__ W twist(W v, uint32_t rbrv, uint32_t t, const W *__restrict__ pw, const ModC<W> &c)
+__device__ __forceinline__ W twist(W v, uint32_t s, uint32_t t, const ColArgs<W> &a)
 {
-    const uint32_t e = (rbrv * t) & ((1u << L) - 1u);
-    const W z = __ldg(pw + 2 * (size_t)e), zp = __ldg(pw + 2 * (size_t)e + 1);
-    return shoup<W>(v, z, zp, c.m);
+    const uint32_t l = t & 31u;
+    const uint32_t e = (s * (t - l)) & ((1u << L) - 1u);
+    const W z0 = __ldg(a.pw + 2 * (size_t)e), z0p = __ldg(a.pw + 2 * (size_t)e + 1);
+    const size_t i = (size_t)s * 32 + l;
+    const W z1 = __ldg(a.pwl + 2 * i), z1p = __ldg(a.pwl + 2 * i + 1);
+    return shoup<W>(shoup<W>(v, z1, z1p, a.c.m), z0, z0p, a.c.m);
 }
 
 template <int BITS>
@@ -667,7 +676,7 @@ __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArg
     if (idx >= a.npairs << LR) return;
     const long long pw = idx >> LR;
     const uint32_t col = (uint32_t)idx & ((1u << LR) - 1u);
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < NS; ++s) {
         const W *src;
         if constexpr (SRC == 1) {
@@ -683,8 +692,13 @@ __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArg
         col_fwd_levels<W, L, LR, L - LR - 1>(v, a.tw, a.c);
         if constexpr (TWIST) {
 #pragma unroll
-            for (int k = 0; k < RC; ++k)
-                v[k] = csub<W>(twist<W, L>(v[k], brv_c32<L - LR>((uint32_t)k), col, a.pw, a.c), a.c.m);
+            for (int k = 0; k < RC; ++k) {
+                v[k] = csub<W>(twist<W, L>(v[k], brv_c32<L - LR>((uint32_t)k), col, a), a.c.m);
+                // 64-bit words: keep the compiler from hoisting every table
+                // load ahead of the products (it spills them otherwise)
+                if constexpr (sizeof(W) == 8 && RC > 8)
+                    if ((k & 7) == 7) asm volatile("" ::: "memory");
+            }
         }
 #pragma unroll
         for (int k = 0; k < RC; ++k) dst[col + ((uint32_t)k << LR)] = v[k];
@@ -713,7 +727,11 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
     for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
     if constexpr (TWIST) {
 #pragma unroll
-        for (int k = 0; k < RC; ++k) v[k] = twist<W, L>(v[k], brv_c32<LC>((uint32_t)k), col, a.pw, a.c);
+        for (int k = 0; k < RC; ++k) {
+            v[k] = twist<W, L>(v[k], brv_c32<LC>((uint32_t)k), col, a);
+            if constexpr (sizeof(W) == 8 && RC > 8)
+                if ((k & 7) == 7) asm volatile("" ::: "memory");
+        }
     }
     colg_levels<W, LC, 0, 0, 0, TW_GLOBAL, RC>(v, 0u, a.tw, a.c);
 #pragma unroll
@@ -752,7 +770,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ Co
             const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
 #pragma unroll
             for (int k = 0; k < RC; ++k)
-                v[k] = csub<W>(twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a.pw, a.c), a.c.m);
+                v[k] = csub<W>(twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a), a.c.m);
         }
 #pragma unroll
         for (int k = 0; k < RC; ++k) p[base + ((uint32_t)k << BLO)] = v[k];
@@ -778,7 +796,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_inv(const __grid_constant__ Co
         const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
 #pragma unroll
         for (int k = 0; k < RC; ++k)
-            v[k] = twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a.pw, a.c);
+            v[k] = twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a);
     }
     colg_levels<W, LB, 0, 0, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
 #pragma unroll
