@@ -312,6 +312,7 @@ def run_ours(args):
     }
     if tuned:
         out["config"]["schedule"] = {"pairs_per_wave": tuned["wave"], "heuristic": tuned["default_wave"],
+                                     "twist": bool(tuned["twist"]), "heuristic_twist": bool(tuned["default_twist"]),
                                      "tuned_ms": round(tuned["ms"], 4), "heuristic_ms": round(tuned["default_ms"], 4)}
 
     if not args.quick:
@@ -568,7 +569,8 @@ def run_uneven(args, world, rank, local):
     for k in range(15, 20):                          # split-path classes: autotune pairs per wave
         cnt = int((lens == (1 << k)).sum())
         if cnt:
-            schedule[f"2^{k}"] = ntt.ntt_autotune(M, 1 << k, cnt)["wave"]
+            t = ntt.ntt_autotune(M, 1 << k, cnt)
+            schedule[f"2^{k}"] = {"wave": t["wave"], "twist": bool(t["twist"])}
     bp = ntt.BatchPlan(M, triples)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):

@@ -102,7 +102,7 @@ typedef struct {
     uint32_t word_bits;  /* 32 or 64 */
     uint32_t four_step;  /* 1 when N exceeds one thread block and the split path is used */
     uint32_t wave;       /* pairs per scratch wave of the split path (0 if unused) */
-    uint32_t reserved;
+    uint32_t twist;      /* 1 when the split path of convolutions uses the four-step twist form */
 } ntt_plan_info_t;
 
 /* Fill *info with the plan's parameters.  Errors: NTT_ERR_ARG. */
@@ -191,15 +191,18 @@ void ntt_batch_destroy(ntt_batch_t batch);
 typedef struct {
     uint32_t wave;          /* chosen pairs per scratch wave (split path) */
     uint32_t default_wave;  /* the heuristic choice (4 rows per SM per wave) */
-    double ms;              /* time of one convolution call over `batch` pairs with `wave` */
-    double default_ms;      /* the same with the heuristic wave (0 if not measured) */
+    uint32_t twist;         /* chosen form: 1 the four-step twist, 0 row-dependent twiddles */
+    uint32_t default_twist; /* the heuristic form */
+    double ms;              /* time of one convolution call over `batch` pairs with the choice */
+    double default_ms;      /* the same with the heuristic wave and form (0 if not measured) */
 } ntt_tune_result;
 
-/* Time the split path's candidate schedules (pairs per scratch wave: powers
- * of two, the heuristic, all pairs) for `batch` pairs of length N modulo m
- * on the current GPU, and record the fastest for (GPU name, word size,
- * log2 N); plans created afterwards use it.  Lengths that fit one block
- * have no schedule to choose and return the default.  Synchronous;
+/* Time the split path's candidate schedules -- both forms (the four-step
+ * twist, or row-dependent twiddles) times the pairs per scratch wave
+ * (powers of two, the heuristic, all pairs) -- for `batch` pairs of length
+ * N modulo m on the current GPU, and record the fastest for (GPU name, word
+ * size, log2 N); plans created afterwards use it.  Lengths that fit one
+ * block have no schedule to choose and return the default.  Synchronous;
  * allocates its own buffers.  Errors: as ntt_plan, NTT_ERR_OOM, NTT_ERR_CUDA. */
 ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tune_result *out);
 

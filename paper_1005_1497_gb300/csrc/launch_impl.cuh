@@ -93,18 +93,31 @@ int Launch<W>::pairs_per_block(int L)
     return BLOCK / (32 << (L - RW));
 }
 
-// Rows of a convolution's split path: after the twist of the column pass
-// they are whole length-2^LR convolutions (forward, pointwise, inverse) with
-// the uniform table, so one kernel serves every L; output lazy, natural order.
-template <typename W>
-static cudaError_t launch_conv_rows(const RowArgs<W> &a, int grid, cudaStream_t st)
+// Rows of a convolution's split path.  Untwisted: one row of 2^LR of the
+// length-2^L tree, node twiddles from the plan's table (they depend on the
+// row).  Twisted: after the twist of the column pass the rows are whole
+// length-2^LR convolutions with the uniform table, so one kernel serves
+// every L; output lazy, natural order.
+template <typename W, int L>
+static cudaError_t launch_conv_rows(bool twisted, const RowArgs<W> &a, int grid, cudaStream_t st)
 {
     constexpr int LR = LRMax<W>::v;
-    constexpr size_t smem = CRShape<W, LR, LR>::smem;
-    static const cudaError_t init = ensure_smem(k_conv_cr<W, LR, LR, 0, 1>, smem);
-    if (init != cudaSuccess) return init;
-    k_conv_cr<W, LR, LR, 0, 1><<<grid, BLOCK, smem, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (L > LR && L <= Launch<W>::LMAX) {
+        if (twisted) {
+            constexpr size_t smem = CRShape<W, LR, LR>::smem;
+            static const cudaError_t init = ensure_smem(k_conv_cr<W, LR, LR, 0, 1>, smem);
+            if (init != cudaSuccess) return init;
+            k_conv_cr<W, LR, LR, 0, 1><<<grid, BLOCK, smem, st>>>(a);
+        } else {
+            constexpr size_t smem = CRShape<W, L, LR>::smem;
+            static const cudaError_t init = ensure_smem(k_conv_cr<W, L, LR, 0>, smem);
+            if (init != cudaSuccess) return init;
+            k_conv_cr<W, L, LR, 0><<<grid, BLOCK, smem, st>>>(a);
+        }
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <typename W, int L>
@@ -133,16 +146,16 @@ template <typename W, int L> struct ColSplit {
     static constexpr int TOPLR = LR + LB;                // "row" bits seen by the top pass
 };
 
-template <typename W, int L, int NS, int SRC>
+template <typename W, int L, int NS, int SRC, bool TW>
 static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
 {
     using CS = ColSplit<W, L>;
     if constexpr (L > CS::LR && L <= Launch<W>::LMAX) {
         const long long threads = a.npairs << CS::TOPLR;
-        k_cols_fwd<W, L, CS::TOPLR, NS, SRC, NS == 2 && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
+        k_cols_fwd<W, L, CS::TOPLR, NS, SRC, TW && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         if constexpr (CS::TWO) {
             const long long t2 = a.npairs << (L - CS::LB);
-            k_cols_mid_fwd<W, L, CS::LR, CS::LB, NS><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
+            k_cols_mid_fwd<W, L, CS::LR, CS::LB, NS, TW><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
         }
         return cudaGetLastError();
     } else {
@@ -150,17 +163,17 @@ static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
     }
 }
 
-template <typename W, int L, int DST>
+template <typename W, int L, int DST, bool TW>
 static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
 {
     using CS = ColSplit<W, L>;
     if constexpr (L > CS::LR && L <= Launch<W>::LMAX) {
         if constexpr (CS::TWO) {
             const long long t2 = a.npairs << (L - CS::LB);
-            k_cols_mid_inv<W, L, CS::LR, CS::LB><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
+            k_cols_mid_inv<W, L, CS::LR, CS::LB, TW><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
         }
         const long long threads = a.npairs << CS::TOPLR;
-        k_cols_inv<W, L, CS::TOPLR, DST, !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
+        k_cols_inv<W, L, CS::TOPLR, DST, TW && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;
@@ -219,10 +232,11 @@ cudaError_t Launch<W>::conv_full(int L, int src, const RowArgs<W> &a, int grid, 
 }
 
 template <typename W>
-cudaError_t Launch<W>::conv_rows_split(int L, const RowArgs<W> &a, int grid, cudaStream_t st)
+cudaError_t Launch<W>::conv_rows_split(int L, bool twisted, const RowArgs<W> &a, int grid, cudaStream_t st)
 {
-    if (L <= LRMAX || L > LMAX) return cudaErrorInvalidValue;
-    return launch_conv_rows<W>(a, grid, st);
+#define C(X) launch_conv_rows<W, X>(twisted, a, grid, st)
+    NTT_SWITCH_L(C)
+#undef C
 }
 
 template <typename W>
@@ -234,18 +248,26 @@ cudaError_t Launch<W>::rows_fwd(int L, const RowArgs<W> &a, int grid, cudaStream
 }
 
 template <typename W>
-cudaError_t Launch<W>::cols_fwd(int L, int ns, int src, const ColArgs<W> &a, cudaStream_t st)
+cudaError_t Launch<W>::cols_fwd(int L, int ns, int src, bool twisted, const ColArgs<W> &a, cudaStream_t st)
 {
-    if (ns == 2 && src == 0) {
-#define C(X) launch_cols_fwd<W, X, 2, 0>(a, st)
+    if (ns == 2 && src == 0 && twisted) {
+#define C(X) launch_cols_fwd<W, X, 2, 0, true>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (ns == 2 && src == 0) {
+#define C(X) launch_cols_fwd<W, X, 2, 0, false>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (ns == 2 && src == 1 && twisted) {
+#define C(X) launch_cols_fwd<W, X, 2, 1, true>(a, st)
         NTT_SWITCH_L(C)
 #undef C
     } else if (ns == 2 && src == 1) {
-#define C(X) launch_cols_fwd<W, X, 2, 1>(a, st)
+#define C(X) launch_cols_fwd<W, X, 2, 1, false>(a, st)
         NTT_SWITCH_L(C)
 #undef C
-    } else if (ns == 1 && src == 0) {
-#define C(X) launch_cols_fwd<W, X, 1, 0>(a, st)
+    } else if (ns == 1 && src == 0 && !twisted) {
+#define C(X) launch_cols_fwd<W, X, 1, 0, false>(a, st)
         NTT_SWITCH_L(C)
 #undef C
     }
@@ -253,14 +275,22 @@ cudaError_t Launch<W>::cols_fwd(int L, int ns, int src, const ColArgs<W> &a, cud
 }
 
 template <typename W>
-cudaError_t Launch<W>::cols_inv(int L, int dst, const ColArgs<W> &a, cudaStream_t st)
+cudaError_t Launch<W>::cols_inv(int L, int dst, bool twisted, const ColArgs<W> &a, cudaStream_t st)
 {
-    if (dst == 1) {
-#define C(X) launch_cols_inv<W, X, 1>(a, st)
+    if (dst == 1 && twisted) {
+#define C(X) launch_cols_inv<W, X, 1, true>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (dst == 1) {
+#define C(X) launch_cols_inv<W, X, 1, false>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (twisted) {
+#define C(X) launch_cols_inv<W, X, 0, true>(a, st)
         NTT_SWITCH_L(C)
 #undef C
     }
-#define C(X) launch_cols_inv<W, X, 0>(a, st)
+#define C(X) launch_cols_inv<W, X, 0, false>(a, st)
     NTT_SWITCH_L(C)
 #undef C
 }

@@ -83,6 +83,7 @@ struct ntt_plan_s {
     bool split = false;
     int LR = 0;
     uint32_t wave = 0;                 // pairs per scratch wave (split path)
+    bool twist = false;                // split path form: the four-step twist (else row-dependent twiddles)
     void *scratch = nullptr;           // 2 * wave * N words
     void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
     void *pwl = nullptr;               // split path: (w^(s l), quotient) at s 32 + l, s < 2^(L - LR), l < 32
@@ -192,8 +193,16 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         // Enough pairs per wave to fill every SM with rows several times over,
         // while the scratch (2 N words per pair) stays a few tens of MB.
         const uint64_t rows_per_pair = 1ull << (L - p->LR);
-        uint64_t wave = ntt_tuned_wave(word, L);       // autotuned schedule, if any
+        uint32_t tuned_wave = 0;
+        int tuned_twist = -1;
+        ntt_tuned_schedule(word, L, &tuned_wave, &tuned_twist);      // autotuned schedule, if any
+        uint64_t wave = tuned_wave;
         if (wave == 0) wave = (uint64_t)p->nsm * 4 / rows_per_pair;
+        // Form: the twist wins for 64-bit words and for few column bits
+        // (measured on GB300: u64 2^16 -23%, u64 2^18 -15%, u32 2^15 -4%,
+        // u32 2^19 +19%); the autotuner measures both.
+        p->twist = tuned_twist >= 0 ? tuned_twist != 0 : (word == 64 || L - p->LR <= 2);
+        if (const char *env = getenv("NTT_SPLIT_TWIST")) p->twist = atoi(env) != 0;   // explicit override
         if (wave < 1) wave = 1;
         p->wave = (uint32_t)wave;
         if (cudaMalloc(&p->scratch, 2 * wave * N * elt) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: scratch");
@@ -242,6 +251,7 @@ extern "C" ntt_status ntt_plan_get_info(ntt_plan_t p, ntt_plan_info_t *info)
     info->m = p->m; info->N = p->N; info->log2N = (uint32_t)p->L; info->n_max = p->n_max;
     info->omega = p->omega; info->n_inv = p->n_inv; info->word_bits = (uint32_t)p->word;
     info->four_step = p->split ? 1u : 0u; info->wave = p->wave;
+    info->twist = p->split && p->twist ? 1u : 0u;
     return NTT_OK;
 }
 
@@ -264,8 +274,10 @@ static int row_grid(int nsm, long long rows, int per_block)
 // 1 descriptor list (descs, pair0 offsets into it).
 template <typename W>
 static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, const DevDesc<W> *descs,
-                                 long long pair0, long long batch, W *scratch, uint32_t wave, cudaStream_t st)
+                                 long long pair0, long long batch, W *scratch, uint32_t wave, cudaStream_t st,
+                                 int twist = -1)
 {
+    const bool tw_form = twist < 0 ? p->twist : twist != 0;
     const ModC<W> &c = modc<W>(p);
     const W *tw = (const W *)p->tw;
     const int mode = descs ? 1 : 0;
@@ -278,13 +290,13 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
         const long long np = std::min<long long>(wave, batch - w0);
         ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c, (const W *)p->pw,
                       (const W *)p->pwl};
-        cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, ca, st);
+        cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, tw_form, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);
         RowArgs<W> ra{scratch, scratch + (size_t)wave * N, scratch, nullptr, rows, 0, tw, c};
-        e = Launch<W>::conv_rows_split(p->L, ra, row_grid(p->nsm, rows, Launch<W>::pairs_per_block(p->LR)), st);
+        e = Launch<W>::conv_rows_split(p->L, tw_form, ra, row_grid(p->nsm, rows, Launch<W>::pairs_per_block(p->LR)), st);
         if (e != cudaSuccess) return e;
-        e = Launch<W>::cols_inv(p->L, mode, ca, st);
+        e = Launch<W>::cols_inv(p->L, mode, tw_form, ca, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -305,7 +317,7 @@ static cudaError_t ntt_dispatch(ntt_plan_t p, const W *x, W *y, long long batch,
     for (long long w0 = 0; w0 < batch; w0 += wave) {
         const long long np = std::min<long long>(wave, batch - w0);
         ColArgs<W> ca{x, nullptr, nullptr, scratch, nullptr, nullptr, np, w0, tw, c};
-        cudaError_t e = Launch<W>::cols_fwd(p->L, 1, 0, ca, st);
+        cudaError_t e = Launch<W>::cols_fwd(p->L, 1, 0, false, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);
         RowArgs<W> ra{scratch, nullptr, nullptr, nullptr, rows, 0, tw, c};
@@ -445,15 +457,15 @@ ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs, long long count, void
 }
 
 ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, void *h, long long batch,
-                                 void *scratch, uint32_t wave, cudaStream_t st)
+                                 void *scratch, uint32_t wave, cudaStream_t st, int twist)
 {
     if (!p || !f || !g || !h || batch <= 0) return ntt_fail(NTT_ERR_ARG, "conv (scratch): invalid argument");
     if (p->split && (!scratch || wave == 0)) return ntt_fail(NTT_ERR_ARG, "conv (scratch): split path needs scratch");
     cudaError_t e = p->word == 32
         ? conv_dispatch<uint32_t>(p, (const uint32_t *)f, (const uint32_t *)g, (uint32_t *)h, nullptr, 0, batch,
-                                  (uint32_t *)scratch, wave, st)
+                                  (uint32_t *)scratch, wave, st, twist)
         : conv_dispatch<uint64_t>(p, (const uint64_t *)f, (const uint64_t *)g, (uint64_t *)h, nullptr, 0, batch,
-                                  (uint64_t *)scratch, wave, st);
+                                  (uint64_t *)scratch, wave, st, twist);
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (scratch)");
 }
 

@@ -17,9 +17,10 @@ ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs_dev, long long count, 
 // Fused convolution of contiguous [batch][N] arrays with caller-chosen
 // split-path scratch (wave pairs of 2 N words); scratch unused when N fits one block.
 ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, void *h, long long batch,
-                                 void *scratch, uint32_t wave, cudaStream_t st);
+                                 void *scratch, uint32_t wave, cudaStream_t st, int twist = -1);   // twist: -1 the plan's form, 0 / 1 forced
 // Tuned pairs per scratch wave for (word size, log2 N) on the current GPU, 0 if untuned.
-uint32_t ntt_tuned_wave(int word_bits, int log2N);
+// the autotuned split-path schedule for (this GPU, word size, log2 N); false if none
+bool ntt_tuned_schedule(int word_bits, int log2N, uint32_t *wave, int *twist);
 // Device twiddle table of a plan, and its arithmetic constants (ModC<W> of
 // the plan's word size copied to out, `bytes` bytes).
 // One persistent launch of the whole-sequence fused bodies over a work list

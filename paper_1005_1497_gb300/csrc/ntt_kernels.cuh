@@ -590,7 +590,10 @@ template <typename W> struct ColArgs {
     const W *pwl;       // (w^(s l), quotient) at s 32 + l, s < 2^(L-LR), l < 32
 };
 
-// The four-step twist of a convolution's split path.  After the column
+// The four-step twist, one of the two forms of a convolution's split path
+// (the plan picks one per word size and length; the autotuner measures
+// both).  In the other form the rows read their node twiddles, which then
+// depend on the row, from the plan's table.  With the twist: after the column
 // levels, element (r, t) -- r the top L - LR index bits at their tree
 // position, t the low LR bits -- is multiplied by w^(brv(r) t).  That turns
 // every row's remaining levels into the length-2^LR transform with the
@@ -748,7 +751,7 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
 // register bit J is x >> (BLO + J + 1) = (hi << (LB - J - 1)) | (k >> (J + 1)),
 // so a column's twiddles depend on its top bits hi (read from the plan's
 // table).  Forward: after the top bits; inverse (transposed): before them.
-template <typename W, int L, int BLO, int LB, int NS>
+template <typename W, int L, int BLO, int LB, int NS, bool TWIST>
 __global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int RC = 1 << LB, LO = L - LB;           // LO: bits outside the register group
@@ -766,7 +769,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ Co
 #pragma unroll
         for (int k = 0; k < RC; ++k) v[k] = p[base + ((uint32_t)k << BLO)];
         colf_levels<W, LB, 0, LB - 1, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
-        if constexpr (NS == 2) {                      // convolutions: the twist (brv over all L - BLO top bits)
+        if constexpr (TWIST) {                        // the twist (brv over all L - BLO top bits)
             const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
 #pragma unroll
             for (int k = 0; k < RC; ++k)
@@ -777,7 +780,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ Co
     }
 }
 
-template <typename W, int L, int BLO, int LB>
+template <typename W, int L, int BLO, int LB, bool TWIST>
 __global__ void __launch_bounds__(256) k_cols_mid_inv(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int RC = 1 << LB, LO = L - LB;
@@ -792,7 +795,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_inv(const __grid_constant__ Co
     W v[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) v[k] = p[base + ((uint32_t)k << BLO)];
-    {
+    if constexpr (TWIST) {
         const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
 #pragma unroll
         for (int k = 0; k < RC; ++k)

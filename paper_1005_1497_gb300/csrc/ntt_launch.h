@@ -18,9 +18,10 @@ template <typename W> struct Launch {
     static cudaError_t conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st);
     // split path pieces (LRMAX < L <= LMAX); cols_fwd / cols_inv run one or
     // two column passes
-    static cudaError_t conv_rows_split(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
-    static cudaError_t cols_fwd(int L, int ns, int src, const ColArgs<W> &a, cudaStream_t st);
-    static cudaError_t cols_inv(int L, int dst, const ColArgs<W> &a, cudaStream_t st);
+    // (twisted: the four-step twist form, see the twist in ntt_kernels.cuh)
+    static cudaError_t conv_rows_split(int L, bool twisted, const RowArgs<W> &a, int grid, cudaStream_t st);
+    static cudaError_t cols_fwd(int L, int ns, int src, bool twisted, const ColArgs<W> &a, cudaStream_t st);
+    static cudaError_t cols_inv(int L, int dst, bool twisted, const ColArgs<W> &a, cudaStream_t st);
     static cudaError_t rows_fwd(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
     static cudaError_t bitrev_out(int L, bool inv, const W *src, W *dst, long long batch, const ModC<W> &c,
                                   cudaStream_t st);

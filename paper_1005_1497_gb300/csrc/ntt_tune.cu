@@ -1,8 +1,9 @@
-// ntt_tune.cu -- autotuner of the split path's schedule: how many pairs a
-// scratch wave carries (bigger waves fill the SMs with more rows and amortise
-// the column passes; smaller ones keep the scratch resident in L2).  The
-// winner is kept per (GPU name, word size, log2 N) in a process-wide table
-// that ntt_plan consults, and can be saved to / loaded from a JSON file.
+// ntt_tune.cu -- autotuner of the split path's schedule: its form (the
+// four-step twist, or row-dependent twiddles) and how many pairs a scratch
+// wave carries (bigger waves fill the SMs with more rows and amortise the
+// column passes; smaller ones keep the scratch resident in L2).  The winner
+// is kept per (GPU name, word size, log2 N) in a process-wide table that
+// ntt_plan consults, and can be saved to / loaded from a JSON file.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +22,7 @@ namespace {
 
 struct Entry {
     uint32_t wave;
+    int twist;
     double ms;
 };
 
@@ -37,12 +39,15 @@ std::string gpu_name()
 
 }  // namespace
 
-uint32_t ntt_tuned_wave(int word_bits, int log2N)
+bool ntt_tuned_schedule(int word_bits, int log2N, uint32_t *wave, int *twist)
 {
     const std::string name = gpu_name();
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_table.find(std::make_tuple(name, word_bits, log2N));
-    return it == g_table.end() ? 0u : it->second.wave;
+    if (it == g_table.end()) return false;
+    *wave = it->second.wave;
+    *twist = it->second.twist;
+    return true;
 }
 
 extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tune_result *out)
@@ -56,6 +61,8 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
     ntt_plan_get_info(p, &info);
     out->default_wave = info.wave;
     out->wave = info.wave;
+    out->default_twist = info.twist;
+    out->twist = info.twist;
     if (!info.four_step) {                       // one block per sequence: nothing to choose
         ntt_plan_destroy(p);
         return NTT_OK;
@@ -90,31 +97,36 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     double best = 1e30, dflt = 0;
     uint32_t best_w = info.wave;
+    int best_tw = (int)info.twist;
     for (uint32_t w : cand) {
         void *scratch = nullptr;
         if (cudaMalloc(&scratch, 2 * (size_t)w * seq) != cudaSuccess) continue;   // too big: skip candidate
-        ntt_status r = ntt_conv_with_scratch(p, f, g, h, (long long)batch, scratch, w, st);
-        float ms = 0;
-        double t = 1e30;
-        if (r == NTT_OK) {
-            cudaEventRecord(e0, st);
-            for (int i = 0; i < 3 && r == NTT_OK; ++i) r = ntt_conv_with_scratch(p, f, g, h, (long long)batch, scratch, w, st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) == cudaSuccess && r == NTT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
-                t = ms / 3.0;
+        for (int tw = 0; tw < 2; ++tw) {
+            ntt_status r = ntt_conv_with_scratch(p, f, g, h, (long long)batch, scratch, w, st, tw);
+            float ms = 0;
+            double t = 1e30;
+            if (r == NTT_OK) {
+                cudaEventRecord(e0, st);
+                for (int i = 0; i < 3 && r == NTT_OK; ++i)
+                    r = ntt_conv_with_scratch(p, f, g, h, (long long)batch, scratch, w, st, tw);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) == cudaSuccess && r == NTT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    t = ms / 3.0;
+            }
+            if (w == info.wave && tw == (int)info.twist) dflt = t;
+            if (t < best) { best = t; best_w = w; best_tw = tw; }
         }
         cudaFree(scratch);
-        if (w == info.wave) dflt = t;
-        if (t < best) { best = t; best_w = w; }
     }
     cleanup();
     if (best >= 1e30) return ntt_fail(NTT_ERR_CUDA, "ntt_autotune: no candidate ran");
     out->wave = best_w;
+    out->twist = (uint32_t)best_tw;
     out->ms = best;
     out->default_ms = dflt;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_table[std::make_tuple(gpu_name(), (int)info.word_bits, (int)info.log2N)] = Entry{best_w, best};
+        g_table[std::make_tuple(gpu_name(), (int)info.word_bits, (int)info.log2N)] = Entry{best_w, best_tw, best};
     }
     return NTT_OK;
 }
@@ -128,9 +140,9 @@ extern "C" ntt_status ntt_autotune_save(const char *path)
     fprintf(fp, "{\"schedules\": [\n");
     size_t i = 0;
     for (auto &kv : g_table) {
-        fprintf(fp, "  {\"gpu\": \"%s\", \"word_bits\": %d, \"log2N\": %d, \"wave\": %u, \"ms\": %.6f}%s\n",
+        fprintf(fp, "  {\"gpu\": \"%s\", \"word_bits\": %d, \"log2N\": %d, \"wave\": %u, \"twist\": %d, \"ms\": %.6f}%s\n",
                 std::get<0>(kv.first).c_str(), std::get<1>(kv.first), std::get<2>(kv.first), kv.second.wave,
-                kv.second.ms, ++i < g_table.size() ? "," : "");
+                kv.second.twist, kv.second.ms, ++i < g_table.size() ? "," : "");
     }
     fprintf(fp, "]}\n");
     fclose(fp);
@@ -147,7 +159,7 @@ extern "C" ntt_status ntt_autotune_load(const char *path)
     std::lock_guard<std::mutex> lk(g_mu);
     while (fgets(line, sizeof line, fp)) {
         char gpu[256];
-        int word, log2N;
+        int word, log2N, twist;
         unsigned wave;
         double ms;
         const char *q = strstr(line, "{\"gpu\": \"");
@@ -157,9 +169,10 @@ extern "C" ntt_status ntt_autotune_load(const char *path)
         if (!e || (size_t)(e - q) >= sizeof gpu) continue;
         memcpy(gpu, q, (size_t)(e - q));
         gpu[e - q] = 0;
-        if (sscanf(e, "\", \"word_bits\": %d, \"log2N\": %d, \"wave\": %u, \"ms\": %lf", &word, &log2N, &wave, &ms) == 4 &&
-            wave > 0) {
-            g_table[std::make_tuple(std::string(gpu), word, log2N)] = Entry{wave, ms};
+        if (sscanf(e, "\", \"word_bits\": %d, \"log2N\": %d, \"wave\": %u, \"twist\": %d, \"ms\": %lf", &word, &log2N,
+                   &wave, &twist, &ms) == 5 &&
+            wave > 0 && (twist == 0 || twist == 1)) {
+            g_table[std::make_tuple(std::string(gpu), word, log2N)] = Entry{wave, twist, ms};
             ++n;
         }
     }

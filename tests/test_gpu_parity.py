@@ -82,6 +82,31 @@ def test_conv_u32_split(ntt, orc, L):
         assert np.array_equal(h[b][idx.astype(np.int64)], orc.conv_sample(f[b], g[b], M, idx))
 
 
+@pytest.mark.parametrize("m,L", [(M, 15), (M, 17), (M, 19), (M64, 14), (M64, 16), (M64, 19), (M64, 20)])
+@pytest.mark.parametrize("form", ["0", "1"])
+def test_conv_split_forms(ntt, orc, monkeypatch, m, L, form):
+    """Both forms of the split path (row-dependent twiddles; the four-step
+    twist), contiguous and through a batch plan's descriptor list."""
+    monkeypatch.setenv("NTT_SPLIT_TWIST", form)
+    N = 1 << L
+    plan = ntt.Plan(m, N)
+    assert plan.twist == (form == "1")
+    wb = plan.word_bits
+    batch = 3
+    f, g = pairs(m, batch, N, seed=600 + L)
+    h = host(ntt.conv_circular(plan, dev(f, wb), dev(g, wb)))
+    want = ref_conv(orc, f[:1], g[:1], m, plan.omega)
+    assert np.array_equal(h[:1], want)
+    for b in range(1, batch):
+        idx = np.random.default_rng(L + b).integers(0, N, 40, dtype=np.uint64)
+        assert np.array_equal(h[b][idx.astype(np.int64)], orc.conv_sample(f[b], g[b], m, idx))
+    triples = [(dev(f[b], wb), dev(g[b], wb), torch.empty(N, dtype=plan.dtype, device="cuda")) for b in range(batch)]
+    ntt.conv_batched(m, triples)
+    torch.cuda.synchronize()
+    for b in range(batch):
+        assert np.array_equal(host(triples[b][2]), h[b])
+
+
 @pytest.mark.parametrize("L", [0, 1, 3, 4, 5, 8, 12, 13, 14, 15, 16, 18, 19, 20])
 def test_conv_u64(ntt, orc, L):
     N = 1 << L
