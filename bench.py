@@ -663,7 +663,8 @@ def run_serve(args, world, rank, local):
            "latency_us": {"p50": round(stats["p50_us"], 1), "p99": round(stats["p99_us"], 1),
                           "mean": round(stats["mean_us"], 1), "max": round(stats["max_us"], 1)},
            "server": {k: stats[k] for k in ("completed", "rejected", "batches", "max_inflight_batches",
-                                              "peak_pool_bytes")},
+                                              "peak_pool_bytes", "direct")},
+           "io": "pinned host buffers addressed in place by the kernels (no staging copies)",
            "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out), flush=True)

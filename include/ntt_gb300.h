@@ -229,14 +229,22 @@ typedef struct {
     uint32_t streams;       /* batches in flight at once (stream slots) */
     uint32_t max_batch;     /* requests per batch at most */
     uint32_t max_log2N;     /* longest admissible length 2^max_log2N */
-    uint32_t reserved;
+    uint32_t flags;         /* NTT_SERVER_STAGE_ALL: copy every request through the pool */
 } ntt_server_config;
+
+/* Requests whose three buffers the GPU can address (page-locked host memory,
+ * device or managed memory) are "direct": the kernels read f, g and write h
+ * in place through the batch's descriptor list, with no copies and no pool
+ * memory.  Other requests (pageable memory), or all of them with this flag,
+ * are staged: copied into a pool block, convolved, copied back. */
+#define NTT_SERVER_STAGE_ALL 1u
 
 typedef struct {
     uint64_t submitted, completed, rejected, batches;
     uint64_t pool_bytes, peak_pool_bytes;
     uint32_t max_inflight_batches, reserved;
     double p50_us, p99_us, mean_us, max_us;   /* submit -> result in host memory */
+    uint64_t direct;        /* completed requests that ran in place (no pool, no copies) */
 } ntt_server_stats;
 
 /* Create a server for modulus m on the current device (allocates the pool,
@@ -244,11 +252,13 @@ typedef struct {
  * plans).  Errors: as ntt_plan, NTT_ERR_ARG, NTT_ERR_OOM. */
 ntt_status ntt_server_create(uint64_t m, const ntt_server_config *cfg, ntt_server_t *out);
 
-/* Queue h = f (*) g of length N (Eq. 1).  f, g, h are HOST pointers of N
- * words each (page-locked memory gives asynchronous copies) that must stay
- * valid until ntt_server_wait returns for *id.  Thread-safe; returns at once.
+/* Queue h = f (*) g of length N (Eq. 1).  f, g, h are pointers of N words
+ * each -- host memory (page-locked memory runs direct, see above; pageable
+ * memory is staged) or device memory -- that must stay valid until
+ * ntt_server_wait returns for *id.  Thread-safe; returns at once.
  * Errors: NTT_ERR_ARG, NTT_ERR_LENGTH (N above 2^max_log2N),
- * NTT_ERR_ADMISSION (3 N words exceed the whole pool; *id is still set). */
+ * NTT_ERR_ADMISSION (a staged request whose 3 N words exceed the whole pool;
+ * *id is still set). */
 ntt_status ntt_server_submit(ntt_server_t srv, const void *f_host, const void *g_host, void *h_host,
                              uint32_t N, uint64_t *id);
 

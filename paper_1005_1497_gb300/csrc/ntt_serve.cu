@@ -1,9 +1,12 @@
 // ntt_serve.cu -- request loop for convolution serving: requests of
-// different power-of-two lengths arrive from host threads, are admitted
-// against a fixed device-memory pool, batched continuously (a new batch
-// leaves as soon as a stream slot and pool memory are free, while earlier
-// batches still run), convolved by the fused kernels through the resident
-// plans of the library, and copied back; per-request latency is recorded.
+// different power-of-two lengths arrive from host threads and are batched
+// continuously (a new batch leaves as soon as a stream slot is free, while
+// earlier batches still run) and convolved by the fused kernels through the
+// resident plans of the library; per-request latency is recorded.  Requests
+// whose buffers the GPU can address (page-locked host memory over the
+// C2C link, or device memory) run in place: the kernels read and write them
+// through the batch's descriptor list.  Others are admitted against a fixed
+// device-memory pool, copied in, convolved and copied back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -85,7 +88,10 @@ struct Req {
     double t_submit = 0, t_done = 0;
     ntt_status status = NTT_OK;
     bool done = false;
-    size_t off = 0, bytes = 0;          // pool block holding f, g, h on the device
+    size_t off = 0, bytes = 0;          // pool block holding f, g, h on the device (staged)
+    bool direct = false;                // the kernels address f, g, h themselves
+    const void *fd = nullptr, *gd = nullptr;
+    void *hd = nullptr;                 // device-side addresses of f, g, h (direct)
 };
 
 struct Slot {
@@ -114,13 +120,31 @@ struct ntt_server_s {
     std::deque<Req *> pending;
     std::unordered_map<uint64_t, Req *> live;
     std::vector<double> lat_us;
-    uint64_t next_id = 1, submitted = 0, completed = 0, rejected = 0, batches = 0;
+    uint64_t next_id = 1, submitted = 0, completed = 0, rejected = 0, batches = 0, direct = 0;
     uint32_t inflight = 0, max_inflight = 0;
     bool stop = false;
     ntt_status fatal = NTT_OK;
     std::thread worker;
     int device = 0;
 };
+
+// The address at which the kernels of `device` reach p: page-locked host
+// memory (mapped into the unified address space), memory of that device, or
+// managed memory; nullptr when they cannot (pageable memory, another GPU).
+static const void *device_address(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeHost: return at.devicePointer;
+    case cudaMemoryTypeDevice: return at.device == device ? at.devicePointer : nullptr;
+    case cudaMemoryTypeManaged: return at.devicePointer;
+    default: return nullptr;
+    }
+}
 
 static ntt_status server_launch(ntt_server_t s, Slot &slot, std::vector<Req *> &batch)
 {
@@ -132,6 +156,12 @@ static ntt_status server_launch(ntt_server_t s, Slot &slot, std::vector<Req *> &
     void **host = (void **)slot.descs_host;
     for (size_t i = 0; i < batch.size(); ++i) {
         Req *r = batch[i];
+        if (r->direct) {
+            host[3 * i + 0] = const_cast<void *>(r->fd);
+            host[3 * i + 1] = const_cast<void *>(r->gd);
+            host[3 * i + 2] = r->hd;
+            continue;
+        }
         unsigned char *d = base + r->off;
         const size_t seq = (size_t)r->N * elt;
         host[3 * i + 0] = d;
@@ -156,6 +186,7 @@ static ntt_status server_launch(ntt_server_t s, Slot &slot, std::vector<Req *> &
         i = j;
     }
     for (Req *r : batch) {
+        if (r->direct) continue;
         const size_t seq = (size_t)r->N * elt;
         if (cudaMemcpyAsync(r->h, base + r->off + 2 * seq, seq, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return ntt_fail(NTT_ERR_CUDA, "server: output copy");
@@ -183,7 +214,8 @@ static void server_loop(ntt_server_t s)
                 r->status = q == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
                 r->t_done = t;
                 r->done = true;
-                s->pool.release(r->off, r->bytes);
+                if (r->direct) ++s->direct;
+                else s->pool.release(r->off, r->bytes);
                 s->lat_us.push_back(t - r->t_submit);
                 ++s->completed;
             }
@@ -200,11 +232,13 @@ static void server_loop(ntt_server_t s)
             std::vector<Req *> batch;
             while (!s->pending.empty() && batch.size() < s->cfg.max_batch) {
                 Req *r = s->pending.front();
-                const size_t need = 3 * (size_t)r->N * elt;
-                size_t off;
-                if (!s->pool.alloc(need, &off)) break;    // wait for memory to free up
-                r->off = off;
-                r->bytes = need;
+                if (!r->direct) {
+                    const size_t need = 3 * (size_t)r->N * elt;
+                    size_t off;
+                    if (!s->pool.alloc(need, &off)) break;    // wait for memory to free up
+                    r->off = off;
+                    r->bytes = need;
+                }
                 batch.push_back(r);
                 s->pending.pop_front();
             }
@@ -214,7 +248,7 @@ static void server_loop(ntt_server_t s)
                 for (Req *r : batch) {
                     r->status = e;
                     r->done = true;
-                    s->pool.release(r->off, r->bytes);
+                    if (!r->direct) s->pool.release(r->off, r->bytes);
                 }
                 s->fatal = e;
                 s->cv_done.notify_all();
@@ -309,13 +343,21 @@ extern "C" ntt_status ntt_server_submit(ntt_server_t s, const void *f, const voi
     const size_t need = Pool::round(3 * (size_t)N * (s->word / 8));
     Req *r = new Req();
     r->f = f; r->g = g; r->h = h; r->N = N; r->L = L;
+    if (!(s->cfg.flags & NTT_SERVER_STAGE_ALL)) {
+        const void *fd = device_address(f, s->device), *gd = device_address(g, s->device);
+        void *hd = const_cast<void *>(device_address(h, s->device));
+        if (fd && gd && hd) {
+            r->direct = true;
+            r->fd = fd; r->gd = gd; r->hd = hd;
+        }
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     if (id) *id = r->id;
     r->t_submit = now_us();
     ++s->submitted;
     s->live[r->id] = r;
-    if (need > s->pool.size()) {                  // can never be admitted
+    if (!r->direct && need > s->pool.size()) {    // can never be admitted
         r->status = NTT_ERR_ADMISSION;
         r->done = true;
         ++s->rejected;
@@ -364,6 +406,7 @@ extern "C" ntt_status ntt_server_get_stats(ntt_server_t s, ntt_server_stats *out
     out->max_inflight_batches = s->max_inflight;
     out->pool_bytes = s->pool.size();
     out->peak_pool_bytes = s->pool.peak();
+    out->direct = s->direct;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
         std::sort(v.begin(), v.end());
@@ -383,7 +426,7 @@ extern "C" ntt_status ntt_server_reset_stats(ntt_server_t s)
     if (!s) return ntt_fail(NTT_ERR_ARG, "ntt_server_reset_stats: NULL server");
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat_us.clear();
-    s->submitted = s->completed = s->rejected = s->batches = 0;
+    s->submitted = s->completed = s->rejected = s->batches = s->direct = 0;
     s->max_inflight = 0;
     return NTT_OK;
 }

@@ -367,7 +367,7 @@ def ntt_check_range(plan: Plan, x: torch.Tensor, stream=None) -> int:
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("pool_bytes", ctypes.c_uint64), ("streams", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
-                ("max_log2N", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_log2N", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -375,22 +375,26 @@ class ServerStats(ctypes.Structure):
                 ("batches", ctypes.c_uint64), ("pool_bytes", ctypes.c_uint64), ("peak_pool_bytes", ctypes.c_uint64),
                 ("max_inflight_batches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("max_us", ctypes.c_double)]
+                ("max_us", ctypes.c_double), ("direct", ctypes.c_uint64)]
 
 
 class Server:
     """``ntt_server_create``: continuous-batching convolution server (host buffers)."""
 
-    def __init__(self, m: int, pool_bytes: int = 1 << 30, streams: int = 4, max_batch: int = 256, max_log2N: int = 18):
-        cfg = ServerConfig(pool_bytes, streams, max_batch, max_log2N, 0)
+    STAGE_ALL = 1
+
+    def __init__(self, m: int, pool_bytes: int = 1 << 30, streams: int = 4, max_batch: int = 256, max_log2N: int = 18,
+                 flags: int = 0):
+        cfg = ServerConfig(pool_bytes, streams, max_batch, max_log2N, flags)
         h = ctypes.c_void_p()
         _check(lib().ntt_server_create(m, ctypes.byref(cfg), ctypes.byref(h)), "ntt_server_create")
         self.handle = h
         self.m = m
 
     def submit(self, f: torch.Tensor, g: torch.Tensor, h: torch.Tensor) -> int:
-        """Queue h = f (*) g; CPU tensors (pinned for asynchronous copies) that
-        must stay alive until wait() returns.  Returns the request id."""
+        """Queue h = f (*) g; tensors that must stay alive until wait() returns
+        (pinned or CUDA tensors run in place, pageable ones are staged
+        through the pool).  Returns the request id."""
         rid = ctypes.c_uint64(0)
         st = lib().ntt_server_submit(self.handle, f.data_ptr(), g.data_ptr(), h.data_ptr(), f.numel(),
                                      ctypes.byref(rid))

@@ -26,18 +26,22 @@ def _requests(m, count, lo, hi, seed):
 
 
 @pytest.mark.parametrize("m", [M64, M])
-def test_server_mix_equals_alone(m):
+@pytest.mark.parametrize("staged", [False, True])
+def test_server_mix_equals_alone(m, staged):
     need_gpu()
     from paper_1005_1497_gb300 import ntt
     reqs = _requests(m, 160, 8, 16, seed=31)
-    srv = ntt.Server(m, pool_bytes=48 << 20, streams=4, max_batch=32, max_log2N=16)
+    srv = ntt.Server(m, pool_bytes=48 << 20, streams=4, max_batch=32, max_log2N=16,
+                     flags=ntt.Server.STAGE_ALL if staged else 0)
     ids = [srv.submit(f, g, h) for f, g, h, _ in reqs]            # burst: the mix
     for i in ids:
         srv.wait(i)
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["rejected"] == 0
+    assert st["direct"] == (0 if staged else len(reqs))             # pinned buffers run in place
     assert st["max_inflight_batches"] >= 2                          # batches overlapped on the GPU
     assert st["peak_pool_bytes"] <= st["pool_bytes"]
+    assert (st["peak_pool_bytes"] > 0) == staged
     assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
     plans = {}
     o = oracle.Oracle()
@@ -58,7 +62,7 @@ def test_server_mix_equals_alone(m):
 def test_server_admission_and_limits():
     need_gpu()
     from paper_1005_1497_gb300 import ntt
-    srv = ntt.Server(M64, pool_bytes=1 << 20, streams=2, max_batch=8, max_log2N=16)
+    srv = ntt.Server(M64, pool_bytes=1 << 20, streams=2, max_batch=8, max_log2N=16, flags=ntt.Server.STAGE_ALL)
     f = torch.zeros(1 << 16, dtype=torch.int64).pin_memory()
     h = torch.empty_like(f).pin_memory()
     st, rid = srv.submit_raw(f.data_ptr(), f.data_ptr(), h.data_ptr(), 1 << 16)   # 1.5 MiB > 1 MiB pool
@@ -71,4 +75,26 @@ def test_server_admission_and_limits():
     out = torch.empty_like(small).pin_memory()
     srv.wait(srv.submit(small, small, out))
     assert torch.all(out == (1 << 10) % M64)                        # (1 * 1) summed over N terms
+    srv.close()
+
+
+def test_server_pageable_and_device_buffers():
+    """Pageable host buffers are staged through the pool automatically;
+    device buffers run in place; both give the fused path's result."""
+    need_gpu()
+    from paper_1005_1497_gb300 import ntt
+    srv = ntt.Server(M64, pool_bytes=64 << 20, streams=2, max_batch=16, max_log2N=15)
+    reqs = _requests(M64, 12, 10, 15, seed=77)
+    pageable = [(f.clone(), g.clone(), torch.empty_like(h), N) for f, g, h, N in reqs]   # clone() is not pinned
+    assert not pageable[0][0].is_pinned()
+    device = [(f.cuda(), g.cuda(), torch.empty(N, dtype=torch.int64, device="cuda"), N) for f, g, h, N in reqs]
+    torch.cuda.synchronize()
+    ids = [srv.submit(f, g, h) for f, g, h, _ in pageable] + [srv.submit(f, g, h) for f, g, h, _ in device]
+    for i in ids:
+        srv.wait(i)
+    st = srv.stats()
+    assert st["completed"] == 2 * len(reqs) and st["direct"] == len(reqs)
+    for (f, g, h, N), (_, _, hd, _) in zip(pageable, device):
+        ref = ntt.conv_circular(ntt.Plan(M64, N), f.cuda(), g.cuda()).cpu()
+        assert torch.equal(h, ref) and torch.equal(hd.cpu(), ref)
     srv.close()
