@@ -393,13 +393,37 @@ extern "C" ntt_status ntt_check_range(ntt_plan_t p, const void *data, size_t cou
 
 // ------------------------------------------------------- host-buffer path
 
+// The device address of page-locked host memory (mapped into the unified
+// address space); nullptr for anything else.
+static const void *host_device_address(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void *g, void *h, size_t batch,
                                          ntt_stream_t stream)
 {
     if (!p || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular_host: invalid argument");
+    // Page-locked buffers: the kernels read f, g and write h where they are
+    // (over the C2C link), with no staging copies.
+    const void *fd = host_device_address(f), *gd = host_device_address(g);
+    void *hd = const_cast<void *>(host_device_address(h));
+    const char *force = getenv("NTT_HOST_STAGE");
+    if (fd && gd && hd && !(force && atoi(force))) {
+        ntt_status s = conv_circular(p, fd, gd, hd, batch, stream);
+        if (s != NTT_OK) return s;
+        CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "conv_circular_host: sync");
+        return NTT_OK;
+    }
     const size_t elt = p->word / 8;
     const size_t seq = (size_t)p->N * elt;
-    // chunk of ~32 MB of input per pipeline slot, at least one pair
+    // pageable buffers: a two-slot copy/compute pipeline with chunks of
+    // ~32 MB of input per slot, at least one pair
     size_t chunk = std::max<size_t>(1, (size_t)(32u << 20) / (2 * seq));
     chunk = std::min(chunk, batch);
     if (!p->stage || p->stage_pairs < chunk) {
