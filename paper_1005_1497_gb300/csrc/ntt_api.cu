@@ -409,19 +409,26 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
                                          ntt_stream_t stream)
 {
     if (!p || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular_host: invalid argument");
-    // Page-locked buffers: the kernels read f, g and write h where they are
-    // (over the C2C link), with no staging copies.
+    const size_t elt = p->word / 8;
+    const size_t seq = (size_t)p->N * elt;
+    // Page-locked buffers can also be read and written in place by the
+    // kernels over the C2C link.  A share of the pairs (NTT_HOST_DIRECT, in
+    // percent; default 0) goes that way on its own stream while the copy
+    // engines stage the rest.
+    size_t ndirect = 0;
     const void *fd = host_device_address(f), *gd = host_device_address(g);
     void *hd = const_cast<void *>(host_device_address(h));
-    const char *force = getenv("NTT_HOST_STAGE");
-    if (fd && gd && hd && !(force && atoi(force))) {
+    if (fd && gd && hd && !p->split) {
+        const char *env = getenv("NTT_HOST_DIRECT");
+        const int pct = env ? std::max(0, std::min(100, atoi(env))) : 0;
+        ndirect = batch * (size_t)pct / 100;
+    }
+    if (ndirect == batch) {
         ntt_status s = conv_circular(p, fd, gd, hd, batch, stream);
         if (s != NTT_OK) return s;
         CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "conv_circular_host: sync");
         return NTT_OK;
     }
-    const size_t elt = p->word / 8;
-    const size_t seq = (size_t)p->N * elt;
     // pageable buffers: a two-slot copy/compute pipeline with chunks of
     // ~32 MB of input per slot, at least one pair
     size_t chunk = std::max<size_t>(1, (size_t)(32u << 20) / (2 * seq));
@@ -443,10 +450,14 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
     CUDA_TRY(cudaEventRecord(start, user), "record");
     for (int i = 0; i < 2; ++i) CUDA_TRY(cudaStreamWaitEvent(p->hstream[i], start, 0), "wait");
     cudaEventDestroy(start);
+    if (ndirect) {                                  // the in-place share, on the user stream
+        ntt_status s = conv_circular(p, fd, gd, hd, ndirect, stream);
+        if (s != NTT_OK) return s;
+    }
     const unsigned char *fb = (const unsigned char *)f, *gb = (const unsigned char *)g;
     unsigned char *hb = (unsigned char *)h;
     size_t slot = 0;
-    for (size_t b0 = 0; b0 < batch; b0 += chunk, slot ^= 1) {
+    for (size_t b0 = ndirect; b0 < batch; b0 += chunk, slot ^= 1) {
         const size_t nb = std::min(chunk, batch - b0);
         cudaStream_t st = p->split ? p->hstream[0] : p->hstream[slot];   // split path shares scratch
         unsigned char *base = (unsigned char *)p->stage + slot * 3 * chunk * seq;
