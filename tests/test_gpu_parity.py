@@ -268,7 +268,12 @@ def test_check_range(ntt):
     assert ntt.ntt_check_range(plan, x) == 2
 
 
-def test_host_buffers(ntt, orc):
+@pytest.mark.parametrize("direct", ["0", "50", "100"])
+def test_host_buffers(ntt, orc, monkeypatch, direct):
+    """Host buffers: staged through the copy pipeline, in place (page-locked
+    memory addressed by the kernels), or split between the two; pageable
+    buffers are always staged."""
+    monkeypatch.setenv("NTT_HOST_DIRECT", direct)
     for L in (10, 16):
         N = 1 << L
         plan = ntt.Plan(M, N)
@@ -280,6 +285,9 @@ def test_host_buffers(ntt, orc):
         want = host(ntt.conv_circular(plan, ft.cuda(), gt.cuda()))
         assert np.array_equal(ht.numpy().astype(np.uint64), want)
         assert np.array_equal(want[:1], ref_conv(orc, f[:1], g[:1], M, plan.omega))
+        hp = torch.empty_like(ft)                                   # pageable output
+        ntt.conv_circular_host(plan, ft.clone(), gt.clone(), hp)
+        assert np.array_equal(hp.numpy().astype(np.uint64), want)
 
 
 def test_autotune_schedule_roundtrip(ntt, orc, tmp_path):
