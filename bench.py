@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--workload", default="conv2", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="fused timing only (no plain form, e2e, CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--schedule", default=None,
+                    help="split-path schedule file: loaded if it exists (no autotuning), else written after tuning")
     return ap.parse_args()
 
 
@@ -249,7 +251,14 @@ def run_ours(args):
         return run_shift(args, world, rank, local)
     batch, L, desc = WORKLOADS[args.workload]
     N = 1 << L
-    tuned = ntt.ntt_autotune(M, N, batch) if L > 14 else None     # split path: pick pairs per wave
+    tuned = None
+    if L > 14:                                                    # split path: pick form and pairs per wave
+        if args.schedule and os.path.exists(args.schedule):
+            ntt.ntt_autotune_load(args.schedule)
+        else:
+            tuned = ntt.ntt_autotune(M, N, batch)
+            if args.schedule:
+                ntt.ntt_autotune_save(args.schedule)
     plan = ntt.Plan(M, N)
     # inputs from the shared seeded generator (computed on the device), resident in HBM
     seed = 1000 + rank
@@ -566,11 +575,17 @@ def run_uneven(args, world, rank, local):
     h = torch.empty_like(f)
     triples = [(f[o:o + n], g[o:o + n], h[o:o + n]) for o, n in zip(offs.tolist(), lens.tolist())]
     schedule = {}
-    for k in range(15, 20):                          # split-path classes: autotune pairs per wave
-        cnt = int((lens == (1 << k)).sum())
-        if cnt:
-            t = ntt.ntt_autotune(M, 1 << k, cnt)
-            schedule[f"2^{k}"] = {"wave": t["wave"], "twist": bool(t["twist"])}
+    if args.schedule and os.path.exists(args.schedule):
+        ntt.ntt_autotune_load(args.schedule)
+        schedule = {"loaded": args.schedule}
+    else:
+        for k in range(15, 20):                      # split-path classes: autotune form and pairs per wave
+            cnt = int((lens == (1 << k)).sum())
+            if cnt:
+                t = ntt.ntt_autotune(M, 1 << k, cnt)
+                schedule[f"2^{k}"] = {"wave": t["wave"], "twist": bool(t["twist"])}
+        if args.schedule:
+            ntt.ntt_autotune_save(args.schedule)
     bp = ntt.BatchPlan(M, triples)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
