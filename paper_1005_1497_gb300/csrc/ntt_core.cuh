@@ -215,11 +215,17 @@ template <typename W> __host__ __device__ constexpr int tw_per_chunk() { return 
 
 // Load CH (1 or 2 for 32-bit words, 1 for 64-bit words) consecutive pairs
 // starting at index i (aligned to CH).
+// Entry nb + t0 of the table (t0 a constant after unrolling).  The global
+// path forms the 64-bit address of entry nb once and adds t0 as a pointer
+// offset, so that the unrolled loads of one level share one base register
+// and differ by immediates (a 32-bit nb + t0 widened afterwards cannot be
+// split that way, and costs a 64-bit address per load).
 template <typename W, int CH, int TWS>
-__device__ __forceinline__ void load_tw(const W *__restrict__ tw, uint32_t i, W (&z)[CH], W (&zp)[CH])
+__device__ __forceinline__ void load_tw(const W *__restrict__ tw, uint32_t nb, uint32_t t0, W (&z)[CH], W (&zp)[CH])
 {
     constexpr int PC = tw_per_chunk<W>();
     static_assert(CH <= PC, "one chunk at most");
+    const uint32_t i = nb + t0;
     if constexpr (TWS == TW_SMEM) {
         const uint32_t c = tw_swz(i / PC);
         if constexpr (sizeof(W) == 4 && CH == 2) {
@@ -233,14 +239,15 @@ __device__ __forceinline__ void load_tw(const W *__restrict__ tw, uint32_t i, W 
             z[0] = (W)q.x; zp[0] = (W)q.y;
         }
     } else {
+        const W *p = tw + 2 * (size_t)nb;                   // entry nb; + 2 t0 below
         if constexpr (sizeof(W) == 4 && CH == 2) {
-            uint4 q = __ldg(reinterpret_cast<const uint4 *>(tw) + (i >> 1));
+            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p + 2 * (size_t)t0));   // nb + t0 even
             z[0] = (W)q.x; zp[0] = (W)q.y; z[1] = (W)q.z; zp[1] = (W)q.w;
         } else if constexpr (sizeof(W) == 4) {
-            uint2 q = __ldg(reinterpret_cast<const uint2 *>(tw) + i);
+            uint2 q = __ldg(reinterpret_cast<const uint2 *>(p + 2 * (size_t)t0));
             z[0] = (W)q.x; zp[0] = (W)q.y;
         } else {
-            ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(tw) + i);
+            ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(p + 2 * (size_t)t0));
             z[0] = (W)q.x; zp[0] = (W)q.y;
         }
     }
@@ -291,7 +298,7 @@ __device__ __forceinline__ void fwd_level(W (&v)[NS][Geo<W, LR>::R], uint32_t xb
 #pragma unroll
         for (int t0 = 0; t0 < CNT; t0 += CH) {
             W z[CH], zp[CH];
-            load_tw<W, CH, TWS>(tw, nb + t0, z, zp);
+            load_tw<W, CH, TWS>(tw, nb, (uint32_t)t0, z, zp);
 #pragma unroll
             for (int tt = 0; tt < CH; ++tt)
 #pragma unroll
@@ -347,7 +354,7 @@ __device__ __forceinline__ void inv_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
 #pragma unroll
         for (int t0 = 0; t0 < CNT; t0 += CH) {
             W z[CH], zp[CH];
-            load_tw<W, CH, TWS>(tw, nb + t0, z, zp);
+            load_tw<W, CH, TWS>(tw, nb, (uint32_t)t0, z, zp);
 #pragma unroll
             for (int tt = 0; tt < CH; ++tt)
 #pragma unroll
@@ -427,7 +434,7 @@ __device__ __forceinline__ void dit_level(W (&v)[Geo<W, LR>::R], uint32_t xbase,
 #pragma unroll
         for (int t0 = 0; t0 < CNT; t0 += CH) {
             W z[CH], zp[CH];
-            load_tw<W, CH, TWS>(tw, run + t0, z, zp);
+            load_tw<W, CH, TWS>(tw, run, (uint32_t)t0, z, zp);
 #pragma unroll
             for (int tt = 0; tt < CH; ++tt) {
                 const int j = brv_c<JJ>(t0 + tt);         // register bits below JJ

@@ -166,7 +166,7 @@ __device__ __forceinline__ void colf_levels(W (&v)[RR], uint32_t rowbase, const 
 #pragma unroll
             for (int t0 = 0; t0 < CNT; t0 += CH) {
                 W z[CH], zp[CH];
-                load_tw<W, CH, TWS>(tw, nbase + (uint32_t)t0, z, zp);
+                load_tw<W, CH, TWS>(tw, nbase, (uint32_t)t0, z, zp);
 #pragma unroll
                 for (int tt = 0; tt < CH; ++tt)
 #pragma unroll
@@ -204,7 +204,7 @@ __device__ __forceinline__ void colg_levels(W (&v)[RR], uint32_t rowbase, const 
 #pragma unroll
             for (int t0 = 0; t0 < CNT; t0 += CH) {
                 W z[CH], zp[CH];
-                load_tw<W, CH, TWS>(tw, nbase + (uint32_t)t0, z, zp);
+                load_tw<W, CH, TWS>(tw, nbase, (uint32_t)t0, z, zp);
 #pragma unroll
                 for (int tt = 0; tt < CH; ++tt)
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ __forceinline__ void cold_levels(W (&v)[RR], uint32_t tlo, const W *_
 #pragma unroll
         for (int t0 = 0; t0 < CNT; t0 += CH) {
             W z[CH], zp[CH];
-            load_tw<W, CH, TWS>(tw, run + t0, z, zp);
+            load_tw<W, CH, TWS>(tw, run, (uint32_t)t0, z, zp);
 #pragma unroll
             for (int tt = 0; tt < CH; ++tt) {
                 const int j = brv_c<J>(t0 + tt);
@@ -632,7 +632,7 @@ __device__ __forceinline__ void load_tw_run(const W *__restrict__ tw, W (&z)[CNT
 #pragma unroll
     for (int t = 0; t < CNT; ++t) {
         W a[1], ap[1];
-        load_tw<W, 1, TW_GLOBAL>(tw, (uint32_t)t, a, ap);
+        load_tw<W, 1, TW_GLOBAL>(tw, 0u, (uint32_t)t, a, ap);
         z[t] = a[0]; zp[t] = ap[0];
     }
 }
