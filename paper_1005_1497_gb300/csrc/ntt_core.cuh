@@ -23,10 +23,9 @@
 // for ANY input below 2^B, so the forward butterflies never reduce their
 // sums: after d levels every value is below 2 m (d + 1).  The inverse
 // butterflies reduce their sums with one conditional subtraction.  The
-// pointwise product of the fused paths is a Montgomery reduction (R = 2^B)
-// of F G after F is brought below 2m by conditional subtractions, which
-// yields F G R^-1 mod m in [0, 2m); the final canonical reduction is a Shoup
-// product by N^-1 R, which restores the scale.  B is the word width (32/64).
+// pointwise product is a Shoup product by N^-1 2^B followed by a Montgomery
+// reduction (R = 2^B), which yields F G N^-1 mod m in [0, 2m).  Final outputs
+// are reduced to the canonical range [0, m).  B is the word width (32/64).
 //
 // Thread mapping.  A "row" of 2^LR elements is transformed by a group of T
 // threads, each holding R = 2^RL elements in registers.  The levels are
@@ -135,8 +134,8 @@ __device__ __forceinline__ void gs_bfly_one(W &a, W &b, const ModC<W> &c)
     b = d2 < d ? d2 : d;
 }
 
-// Pointwise product F G N^{-1} mod m in [0, 2m) (the plain per-level form):
-// Shoup by N^{-1} 2^B, then a Montgomery reduction of the double-word product.
+// Pointwise product F G N^{-1} mod m in [0, 2m): Shoup by N^{-1} 2^B, then a
+// Montgomery reduction of the double-word product.
 __device__ __forceinline__ uint32_t pointwise(uint32_t F, uint32_t G, const ModC<uint32_t> &c)
 {
     uint32_t u = shoup<uint32_t>(F, c.cN, c.cNp, c.m);
@@ -153,25 +152,6 @@ __device__ __forceinline__ uint64_t pointwise(uint64_t F, uint64_t G, const ModC
     uint64_t hi = __umul64hi(u, G);
     uint64_t q = lo * c.mneg;
     return hi + __umul64hi(q, c.m) + (lo != 0ull ? 1ull : 0ull);
-}
-
-// Pointwise product of the fused paths: F G R^-1 mod m in [0, 2m), R = 2^B,
-// for F, G < 64m (every forward output is below 62m).  Five conditional
-// subtractions (ALU) bring F below 2m, so F G < 128 m^2 < R m and a bare
-// Montgomery reduction stays below 2m; the factor N^-1 R is applied by the
-// final canonical reduction, which is a Shoup product anyway.
-template <typename W>
-__device__ __forceinline__ W pointwise_mont(W F, W G, const ModC<W> &c)
-{
-    W f = csub<W>(F, c.m << 5);
-    f = csub<W>(f, c.m << 4);
-    f = csub<W>(f, c.m << 3);
-    f = csub<W>(f, c.m << 2);
-    f = csub<W>(f, c.m2);
-    const W lo = f * G;
-    const W hi = Arith<W>::mulhi(f, G);
-    const W q = lo * c.mneg;
-    return hi + Arith<W>::mulhi(q, c.m) + (lo != 0 ? (W)1 : (W)0);
 }
 
 // ---------------------------------------------------------------- geometry

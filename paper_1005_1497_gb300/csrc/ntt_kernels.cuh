@@ -109,12 +109,12 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
         }
         fwd_all<W, L, L, 0, 2, TW_SMEM, true>(v, 0u, tau, S, gid, stw, a.c);
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[0][k] = pointwise_mont<W>(v[0][k], v[1][k], a.c);
+        for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[0][k], v[1][k], a.c);
         dit_all<W, L, last, TW_SMEM>(v[0], 0u, tau, S, gid, stw, a.c);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const uint32_t x = b0 + ((uint32_t)k << lo0);
-            hp[(N - x) & (N - 1u)] = canon<W>(v[0][k], a.c.cN, a.c.cNp, a.c.m);      // N^-1 R: see pointwise_mont
+            hp[(N - x) & (N - 1u)] = canon<W>(v[0][k], (W)1, a.c.onep, a.c.m);
         }
     }
 }
@@ -410,7 +410,7 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
         }
         fwd_all<W, L, RW, 0, 2, FTW>(v, rcur + ((uint32_t)wr << RW), lane, Srow, 0, ftw, a.c);
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[0][k] = pointwise_mont<W>(v[1][k], v[0][k], a.c);
+        for (int k = 0; k < R; ++k) v[0][k] = pointwise(v[1][k], v[0][k], a.c);
         if (PREF && rho + stride < (ITEM ? end : a.nrows)) {
             ptrs(rho + stride, fp, gp, hp, rowoff);
             load_cols(fp, v[1]);                            // next row's f
@@ -437,7 +437,7 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
-                if constexpr (FULL && OUT == 0) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], a.c.cN, a.c.cNp, a.c.m);
+                if constexpr (FULL && OUT == 0) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
                 else hcur[x] = v[0][j * RC + k];
             }
     }
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
 #pragma unroll
     for (int k = 0; k < RC; ++k) {
         const uint32_t x = col + ((uint32_t)k << LR);
-        out[(N - x) & (N - 1u)] = canon<W>(v[k], a.c.cN, a.c.cNp, a.c.m);      // N^-1 R: see pointwise_mont
+        out[(N - x) & (N - 1u)] = csub<W>(v[k], a.c.m);
     }
 }
 
