@@ -388,17 +388,25 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
             prefetch_l2(gn, (1u << LROW) * (uint32_t)sizeof(W));
         }
         // forward, column phase: columns c = ptau + j TPP, elements x = c + k 2^RW
+        // (f's columns go to shared memory while g's levels run: measured
+        // 1.4% faster than storing both after both)
         load_cols(gcur, v[0]);
         colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[1], rcur >> RW, ftw, a.c);
-        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[0], rcur >> RW, ftw, a.c);
         psync();                                            // slices free (previous row)
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const uint32_t y = ptau + (uint32_t)j * TPP;
-                P[(size_t)k * 2 * GR::ROWP + GR::pad(y)] = v[0][j * RC + k];
-                P[(size_t)k * 2 * GR::ROWP + GR::ROWP + GR::pad(y)] = v[1][j * RC + k];   // (v[0] = g, v[1] = f)
+                P[(size_t)k * 2 * GR::ROWP + GR::ROWP + GR::pad(y)] = v[1][j * RC + k];   // f
+            }
+        colf_all<W, LC, 0, CPT, L - LROW, FTW, R>(v[0], rcur >> RW, ftw, a.c);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const uint32_t y = ptau + (uint32_t)j * TPP;
+                P[(size_t)k * 2 * GR::ROWP + GR::pad(y)] = v[0][j * RC + k];              // g
             }
         psync();
         // forward, row phase (warp wr owns row wr of this row group)
