@@ -41,6 +41,7 @@ struct PrimeC {
 
 struct ExactArgs {
     int k;                          // number of primes
+    int vec;                        // 1: every base is 16-byte aligned (four-element path)
     long long n;                    // elements
     PrimeC p[KMAX];
     uint64_t inv[KMAX][KMAX];       // inv[i][j] = m_i^-1 mod m_j (i < j)
@@ -65,51 +66,136 @@ __device__ __forceinline__ uint64_t residue(long long x, const PrimeC &p)
     return r;
 }
 
-__global__ void k_exact_residues(const __grid_constant__ ExactArgs a, const long long *__restrict__ x, void *const *out)
+// Four elements per thread (16-byte loads and stores), f and g in one
+// launch; a scalar loop takes the tail and unaligned bases.
+template <int K, typename T>
+__device__ __forceinline__ void put_residues(const ExactArgs &a, void *const *out, long long i, const long long (&x)[4])
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const long long v = x[i];
+    const PrimeC &p = a.p[K];
+    uint64_t r[4];
 #pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            if (j >= a.k) break;
-            const uint64_t r = residue(v, a.p[j]);
-            if (a.p[j].word == 32) static_cast<uint32_t *>(out[j])[i] = (uint32_t)r;
-            else static_cast<uint64_t *>(out[j])[i] = r;
-        }
+    for (int e = 0; e < 4; ++e) r[e] = residue(x[e], p);
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<uint4 *>(static_cast<uint32_t *>(out[K]) + i)[0] =
+            make_uint4((uint32_t)r[0], (uint32_t)r[1], (uint32_t)r[2], (uint32_t)r[3]);
+    } else {
+        ulonglong2 *q = reinterpret_cast<ulonglong2 *>(static_cast<uint64_t *>(out[K]) + i);
+        q[0] = make_ulonglong2(r[0], r[1]);
+        q[1] = make_ulonglong2(r[2], r[3]);
     }
+}
+
+__device__ __forceinline__ void residues_scalar(const ExactArgs &a, const long long *x, void *const *out, long long i)
+{
+    const long long v = x[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j >= a.k) break;
+        const uint64_t r = residue(v, a.p[j]);
+        if (a.p[j].word == 32) static_cast<uint32_t *>(out[j])[i] = (uint32_t)r;
+        else static_cast<uint64_t *>(out[j])[i] = r;
+    }
+}
+
+__global__ void k_exact_residues(const __grid_constant__ ExactArgs a, const long long *__restrict__ f,
+                                 const long long *__restrict__ g, void *const *outf, void *const *outg)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long n4 = a.vec ? a.n / 4 : 0;
+    for (int s = 0; s < 2; ++s) {
+        const long long *x = s == 0 ? f : g;
+        void *const *out = s == 0 ? outf : outg;
+        for (long long q = tid; q < n4; q += nthr) {
+            const longlong2 u0 = reinterpret_cast<const longlong2 *>(x)[2 * q];
+            const longlong2 u1 = reinterpret_cast<const longlong2 *>(x)[2 * q + 1];
+            const long long v[4] = {u0.x, u0.y, u1.x, u1.y};
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j) {
+                if (j >= a.k) break;
+                if (a.p[j].word == 32) {
+                    if (j == 0) put_residues<0, uint32_t>(a, out, 4 * q, v);
+                    else if (j == 1) put_residues<1, uint32_t>(a, out, 4 * q, v);
+                    else if (j == 2) put_residues<2, uint32_t>(a, out, 4 * q, v);
+                    else put_residues<3, uint32_t>(a, out, 4 * q, v);
+                } else {
+                    if (j == 0) put_residues<0, uint64_t>(a, out, 4 * q, v);
+                    else if (j == 1) put_residues<1, uint64_t>(a, out, 4 * q, v);
+                    else if (j == 2) put_residues<2, uint64_t>(a, out, 4 * q, v);
+                    else put_residues<3, uint64_t>(a, out, 4 * q, v);
+                }
+            }
+        }
+        for (long long i = 4 * n4 + tid; i < a.n; i += nthr) residues_scalar(a, x, out, i);
+    }
+}
+
+// Garner's mixed-radix reconstruction of one output from its residues.
+__device__ __forceinline__ long long garner(const ExactArgs &a, const uint64_t (&r)[KMAX])
+{
+    const u128 half = ((u128)a.half_hi << 64) | a.half_lo;
+    const u128 M = ((u128)a.M_hi << 64) | a.M_lo;
+    uint64_t v[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j >= a.k) break;
+        const PrimeC &pj = a.p[j];
+        uint64_t t = r[j];
+        // mixed-radix digit: t = (...((r_j - v_0) c_0j - v_1) c_1j ...) mod m_j
+#pragma unroll
+        for (int q = 0; q < KMAX; ++q) {
+            if (q >= j) break;
+            const uint64_t vq = csub64(shoup64(v[q], 1, pj.onep, pj.m), pj.m);     // v_q mod m_j
+            const uint64_t d = t >= vq ? t - vq : t + pj.m - vq;
+            t = csub64(shoup64(d, a.inv[q][j], a.invp[q][j], pj.m), pj.m);
+        }
+        v[j] = t;
+    }
+    // X = v_0 + m_0 (v_1 + m_1 (v_2 + ...)), Horner from the top digit
+    u128 X = 0;
+#pragma unroll
+    for (int j = KMAX - 1; j >= 0; --j)
+        if (j < a.k) X = X * a.p[j].m + v[j];
+    const i128 s = X > half ? (i128)X - (i128)M : (i128)X;
+    return (long long)s;
+}
+
+__device__ __forceinline__ uint64_t load_res(const ExactArgs &a, void *const *res, int j, long long i)
+{
+    return a.p[j].word == 32 ? (uint64_t) static_cast<const uint32_t *>(res[j])[i] : static_cast<const uint64_t *>(res[j])[i];
 }
 
 __global__ void k_exact_garner(const __grid_constant__ ExactArgs a, void *const *res, long long *__restrict__ h)
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const u128 half = ((u128)a.half_hi << 64) | a.half_lo;
-    const u128 M = ((u128)a.M_hi << 64) | a.M_lo;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        uint64_t v[KMAX];
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long n4 = a.vec ? a.n / 4 : 0;
+    for (long long q = tid; q < n4; q += nthr) {
+        uint64_t r[4][KMAX];
 #pragma unroll
         for (int j = 0; j < KMAX; ++j) {
             if (j >= a.k) break;
-            const PrimeC &pj = a.p[j];
-            uint64_t t = pj.word == 32 ? (uint64_t) static_cast<const uint32_t *>(res[j])[i]
-                                       : static_cast<const uint64_t *>(res[j])[i];
-            // mixed-radix digit: t = (...((r_j - v_0) c_0j - v_1) c_1j ...) mod m_j
-#pragma unroll
-            for (int q = 0; q < KMAX; ++q) {
-                if (q >= j) break;
-                const uint64_t vq = csub64(shoup64(v[q], 1, pj.onep, pj.m), pj.m);     // v_q mod m_j
-                const uint64_t d = t >= vq ? t - vq : t + pj.m - vq;
-                t = csub64(shoup64(d, a.inv[q][j], a.invp[q][j], pj.m), pj.m);
+            if (a.p[j].word == 32) {
+                const uint4 u = reinterpret_cast<const uint4 *>(static_cast<const uint32_t *>(res[j]) + 4 * q)[0];
+                r[0][j] = u.x; r[1][j] = u.y; r[2][j] = u.z; r[3][j] = u.w;
+            } else {
+                const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(static_cast<const uint64_t *>(res[j]) + 4 * q);
+                const ulonglong2 u0 = p[0], u1 = p[1];
+                r[0][j] = u0.x; r[1][j] = u0.y; r[2][j] = u1.x; r[3][j] = u1.y;
             }
-            v[j] = t;
         }
-        // X = v_0 + m_0 (v_1 + m_1 (v_2 + ...)), Horner from the top digit
-        u128 X = 0;
+        longlong2 *o = reinterpret_cast<longlong2 *>(h + 4 * q);
+        o[0] = make_longlong2(garner(a, r[0]), garner(a, r[1]));
+        o[1] = make_longlong2(garner(a, r[2]), garner(a, r[3]));
+    }
+    for (long long i = 4 * n4 + tid; i < a.n; i += nthr) {
+        uint64_t r[KMAX];
 #pragma unroll
-        for (int j = KMAX - 1; j >= 0; --j)
-            if (j < a.k) X = X * a.p[j].m + v[j];
-        const i128 s = X > half ? (i128)X - (i128)M : (i128)X;
-        h[i] = (long long)s;
+        for (int j = 0; j < KMAX; ++j) {
+            if (j >= a.k) break;
+            r[j] = load_res(a, res, j, i);
+        }
+        h[i] = garner(a, r);
     }
 }
 
@@ -270,15 +356,19 @@ extern "C" ntt_status conv_exact(ntt_exact_t e, const int64_t *f, const int64_t 
         a.n = (long long)(np * e->N);
         const int grid = (int)std::min<long long>((a.n + threads - 1) / threads, (long long)e->nsm * 8);
         const size_t off = p0 * e->N;
-        k_exact_residues<<<grid, threads, 0, st>>>(a, (const long long *)f + off, e->ptrs_f);
-        k_exact_residues<<<grid, threads, 0, st>>>(a, (const long long *)g + off, e->ptrs_g);
+        const long long *fw = (const long long *)f + off, *gw = (const long long *)g + off;
+        long long *hw = (long long *)h + off;
+        // scratch bases are 256-byte aligned and hold whole waves, so only the
+        // caller's bases decide the four-element path
+        a.vec = ((((uintptr_t)fw | (uintptr_t)gw | (uintptr_t)hw) & 15u) == 0) ? 1 : 0;
+        k_exact_residues<<<grid, threads, 0, st>>>(a, fw, gw, e->ptrs_f, e->ptrs_g);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: residues: %s", cudaGetErrorString(err));
         for (int i = 0; i < e->k; ++i) {
             ntt_status s = conv_circular(e->plans[i], e->host_ptrs[i], e->host_ptrs[KMAX + i], e->host_ptrs[i], np, stream);
             if (s != NTT_OK) return s;
         }
-        k_exact_garner<<<grid, threads, 0, st>>>(a, e->ptrs_f, (long long *)h + off);
+        k_exact_garner<<<grid, threads, 0, st>>>(a, e->ptrs_f, hw);
         err = cudaGetLastError();
         if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: reconstruction: %s", cudaGetErrorString(err));
     }

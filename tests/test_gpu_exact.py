@@ -109,3 +109,25 @@ def test_conv_exact_many_pairs_in_waves(ntt, orc):
 def test_conv_exact_rejects_uncoverable_bound(ntt):
     with pytest.raises(ntt.NttError):
         ntt.ExactPlan(1 << 20, 63)
+
+
+def test_conv_exact_unaligned_buffers(ntt, orc):
+    """Bases that are not 16-byte aligned take the scalar residue and
+    reconstruction loops; results are the same."""
+    N, bound, batch = 256, 40, 5
+    plan = ntt.ExactPlan(N, bound)
+    amp = amp_for(N, bound)
+    f, g = signed_inputs(batch, N, amp, seed=5)
+    fb = torch.zeros(batch * N + 1, dtype=torch.int64, device="cuda")
+    gb = torch.zeros_like(fb)
+    hb = torch.zeros_like(fb)
+    fb[1:] = torch.from_numpy(f.reshape(-1)).cuda()
+    gb[1:] = torch.from_numpy(g.reshape(-1)).cuda()
+    fv, gv, hv = fb[1:].view(batch, N), gb[1:].view(batch, N), hb[1:].view(batch, N)
+    ntt.conv_exact(plan, fv, gv, out=hv)
+    aligned = ntt.conv_exact(plan, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(hv, aligned)
+    for b in range(batch):
+        assert np.array_equal(hv[b].cpu().numpy(), orc.int_conv(f[b], g[b]))
+    plan.close()
