@@ -667,6 +667,19 @@ def run_serve(args, world, rank, local):
         srv.drain()
         elapsed = time.perf_counter() - t0
     stats = srv.stats()
+    # capacity: the same requests submitted back to back (closed loop, K in flight)
+    srv.reset_stats()
+    ccount = min(count, 20000)
+    t1 = time.perf_counter()
+    cap_ids = [0] * ccount
+    for i in range(ccount):
+        s = i % K
+        if i >= K:
+            srv.wait(cap_ids[i - K])
+        st, cap_ids[i] = srv.submit_raw(fp + 8 * offs[s], gp + 8 * offs[s], hp + 8 * offs[s], int(lens[s]))
+    srv.drain()
+    cap_elapsed = time.perf_counter() - t1
+    cap = srv.stats()
     srv.close()
     mean_n = float(np.mean(lens))
     out = {"metric": METRIC, "value": round(stats["completed"] / elapsed, 1), "unit": "req/s", "n_gpus": world,
@@ -680,6 +693,9 @@ def run_serve(args, world, rank, local):
            "server": {k: stats[k] for k in ("completed", "rejected", "batches", "max_inflight_batches",
                                               "peak_pool_bytes", "direct")},
            "io": "pinned host buffers addressed in place by the kernels (no staging copies)",
+           "capacity": {"req_per_s": round(cap["completed"] / cap_elapsed, 1), "requests": ccount,
+                        "in_flight": K, "p50_us": round(cap["p50_us"], 1), "p99_us": round(cap["p99_us"], 1),
+                        "GBps_host_io": round(24.0 * mean_n * cap["completed"] / cap_elapsed / 1e9, 1)},
            "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out), flush=True)
