@@ -133,8 +133,16 @@ struct ntt_server_s {
 // managed memory; nullptr when they cannot (pageable memory, another GPU).
 static const void *device_address(const void *p, int device)
 {
+    // The query needs the device's context bound to the calling thread (a
+    // client thread may never have touched CUDA); the caller's current
+    // device is restored afterwards.
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = -1;
+    cudaSetDevice(device);
     cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (cur >= 0 && cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
