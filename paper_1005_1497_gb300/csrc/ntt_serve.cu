@@ -266,10 +266,13 @@ static void server_loop(ntt_server_t s)
             ++s->inflight;
             s->max_inflight = std::max(s->max_inflight, s->inflight);
         }
-        // sleep briefly while work is on the GPU; block when idle
+        // While work is on the GPU, poll its events without sleeping (a timed
+        // sleep this short overshoots by tens of microseconds, which the
+        // requests would wait out); a submit also wakes the loop at once.
+        // Block on the condition variable when idle.
         if (s->inflight > 0) {
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            std::this_thread::yield();
             lk.lock();
         } else if (s->pending.empty() && !s->stop) {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
