@@ -123,6 +123,8 @@ struct ntt_server_s {
     uint64_t next_id = 1, submitted = 0, completed = 0, rejected = 0, batches = 0, direct = 0;
     uint32_t inflight = 0, max_inflight = 0;
     bool stop = false;
+    std::atomic<size_t> npending{0};    // pending.size(), readable without the lock
+    std::atomic<bool> stopping{false};  // stop, readable without the lock
     ntt_status fatal = NTT_OK;
     std::thread worker;
     int device = 0;
@@ -200,82 +202,106 @@ static ntt_status server_launch(ntt_server_t s, Slot &slot, std::vector<Req *> &
             return ntt_fail(NTT_ERR_CUDA, "server: output copy");
     }
     if (cudaEventRecord(slot.done, st) != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "server: event");
-    slot.reqs = batch;
-    slot.busy = true;
     return NTT_OK;
 }
 
+// The server thread owns the slots: it queries their events and launches
+// batches without the lock, and takes the lock only to finish completed
+// batches and to take requests out of the queue, so submitting threads are
+// never held up by GPU calls.  While work is on the GPU it polls with a
+// yield (a timed sleep this short overshoots by tens of microseconds, which
+// the requests would wait out); when idle it blocks until a submit.
 static void server_loop(ntt_server_t s)
 {
     cudaSetDevice(s->device);
-    std::unique_lock<std::mutex> lk(s->mu);
     const size_t elt = s->word / 8;
+    std::vector<size_t> ready;
+    std::vector<size_t> to_launch;
+    uint32_t busy = 0;                             // slots with a batch on the GPU (this thread's count)
     while (true) {
-        // completions
-        bool progressed = false;
-        for (Slot &slot : s->slots) {
-            if (!slot.busy) continue;
-            cudaError_t q = cudaEventQuery(slot.done);
-            if (q == cudaErrorNotReady) continue;
-            const double t = now_us();
+        ready.clear();
+        for (size_t i = 0; i < s->slots.size(); ++i)
+            if (s->slots[i].busy && cudaEventQuery(s->slots[i].done) != cudaErrorNotReady) ready.push_back(i);
+        const bool work = !ready.empty() || (s->npending.load(std::memory_order_acquire) > 0 && busy < s->slots.size()) ||
+                          s->stopping.load();
+        if (!work) {
+            if (busy > 0) {
+                std::this_thread::yield();
+            } else {
+                std::unique_lock<std::mutex> lk(s->mu);
+                if (s->pending.empty() && !s->stop) s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            }
+            continue;
+        }
+        to_launch.clear();
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            // completions
+            for (size_t i : ready) {
+                Slot &slot = s->slots[i];
+                const cudaError_t q = cudaEventQuery(slot.done);
+                const double t = now_us();
+                for (Req *r : slot.reqs) {
+                    r->status = q == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
+                    r->t_done = t;
+                    r->done = true;
+                    if (r->direct) ++s->direct;
+                    else s->pool.release(r->off, r->bytes);
+                    s->lat_us.push_back(t - r->t_submit);
+                    ++s->completed;
+                }
+                slot.reqs.clear();
+                slot.busy = false;
+                --s->inflight;
+                --busy;
+            }
+            if (!ready.empty()) s->cv_done.notify_all();
+            if (s->stop && s->pending.empty() && s->inflight == 0) break;
+            // admission: one batch per free slot
+            for (size_t i = 0; i < s->slots.size(); ++i) {
+                Slot &slot = s->slots[i];
+                if (slot.busy || s->pending.empty()) continue;
+                std::vector<Req *> batch;
+                while (!s->pending.empty() && batch.size() < s->cfg.max_batch) {
+                    Req *r = s->pending.front();
+                    if (!r->direct) {
+                        const size_t need = 3 * (size_t)r->N * elt;
+                        size_t off;
+                        if (!s->pool.alloc(need, &off)) break;    // wait for memory to free up
+                        r->off = off;
+                        r->bytes = need;
+                    }
+                    batch.push_back(r);
+                    s->pending.pop_front();
+                    s->npending.fetch_sub(1, std::memory_order_relaxed);
+                }
+                if (batch.empty()) break;
+                slot.reqs = std::move(batch);
+                slot.busy = true;
+                ++s->batches;
+                ++s->inflight;
+                ++busy;
+                s->max_inflight = std::max(s->max_inflight, s->inflight);
+                to_launch.push_back(i);
+            }
+        }
+        // launches, outside the lock
+        for (size_t i : to_launch) {
+            Slot &slot = s->slots[i];
+            const ntt_status e = server_launch(s, slot, slot.reqs);
+            if (e == NTT_OK) continue;
+            std::lock_guard<std::mutex> lk(s->mu);
             for (Req *r : slot.reqs) {
-                r->status = q == cudaSuccess ? NTT_OK : NTT_ERR_CUDA;
-                r->t_done = t;
+                r->status = e;
                 r->done = true;
-                if (r->direct) ++s->direct;
-                else s->pool.release(r->off, r->bytes);
-                s->lat_us.push_back(t - r->t_submit);
-                ++s->completed;
+                if (!r->direct) s->pool.release(r->off, r->bytes);
             }
             slot.reqs.clear();
             slot.busy = false;
             --s->inflight;
-            progressed = true;
-        }
-        if (progressed) s->cv_done.notify_all();
-        if (s->stop && s->pending.empty() && s->inflight == 0) break;
-        // admission and launch: one batch per free slot
-        for (Slot &slot : s->slots) {
-            if (slot.busy || s->pending.empty()) continue;
-            std::vector<Req *> batch;
-            while (!s->pending.empty() && batch.size() < s->cfg.max_batch) {
-                Req *r = s->pending.front();
-                if (!r->direct) {
-                    const size_t need = 3 * (size_t)r->N * elt;
-                    size_t off;
-                    if (!s->pool.alloc(need, &off)) break;    // wait for memory to free up
-                    r->off = off;
-                    r->bytes = need;
-                }
-                batch.push_back(r);
-                s->pending.pop_front();
-            }
-            if (batch.empty()) break;
-            ntt_status e = server_launch(s, slot, batch);
-            if (e != NTT_OK) {
-                for (Req *r : batch) {
-                    r->status = e;
-                    r->done = true;
-                    if (!r->direct) s->pool.release(r->off, r->bytes);
-                }
-                s->fatal = e;
-                s->cv_done.notify_all();
-                continue;
-            }
-            ++s->batches;
-            ++s->inflight;
-            s->max_inflight = std::max(s->max_inflight, s->inflight);
-        }
-        // While work is on the GPU, poll its events without sleeping (a timed
-        // sleep this short overshoots by tens of microseconds, which the
-        // requests would wait out); a submit also wakes the loop at once.
-        // Block on the condition variable when idle.
-        if (s->inflight > 0) {
-            lk.unlock();
-            std::this_thread::yield();
-            lk.lock();
-        } else if (s->pending.empty() && !s->stop) {
-            s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            --busy;
+            s->fatal = e;
+            s->cv_done.notify_all();
         }
     }
 }
@@ -286,6 +312,7 @@ extern "C" void ntt_server_destroy(ntt_server_t s)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        s->stopping.store(true);
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
@@ -375,6 +402,7 @@ extern "C" ntt_status ntt_server_submit(ntt_server_t s, const void *f, const voi
         return ntt_fail(NTT_ERR_ADMISSION, "ntt_server_submit: request needs %zu bytes, pool holds %zu", need, s->pool.size());
     }
     s->pending.push_back(r);
+    s->npending.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_one();
     return NTT_OK;
 }
