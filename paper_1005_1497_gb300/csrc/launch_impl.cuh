@@ -85,6 +85,20 @@ cudaError_t Launch<W>::conv_persistent(const PersistArgs<W> &a, int lmax, int gr
     return launch_persistent<W, LRMax<W>::v>(a, grid, smem, st);
 }
 
+template <typename W, int L, class X>
+static cudaError_t launch_exact(const RowArgs<W> &a, const ExactArgs &e, int grid, cudaStream_t st)
+{
+    if constexpr (L <= LRMax<W>::v) {
+        const size_t smem = full_smem_of<W, L>();
+        static const cudaError_t init = ensure_smem(k_conv_exact<W, L, X>, smem);
+        if (init != cudaSuccess) return init;
+        k_conv_exact<W, L, X><<<grid, BLOCK, smem, st>>>(a, e);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <typename W>
 int Launch<W>::pairs_per_block(int L)
 {
@@ -229,6 +243,19 @@ cudaError_t Launch<W>::conv_full(int L, int src, const RowArgs<W> &a, int grid, 
 #define C0(X) launch_conv_full<W, X, 0>(a, grid, st)
     NTT_SWITCH_L(C0)
 #undef C0
+}
+
+template <typename W>
+cudaError_t Launch<W>::conv_exact(int L, bool garner, const RowArgs<W> &a, const ExactArgs &e, int grid, cudaStream_t st)
+{
+    if (garner) {
+#define C(X) launch_exact<W, X, ExactGarner>(a, e, grid, st)
+        NTT_SWITCH_L(C)
+#undef C
+    }
+#define C(X) launch_exact<W, X, ExactResidues>(a, e, grid, st)
+    NTT_SWITCH_L(C)
+#undef C
 }
 
 template <typename W>

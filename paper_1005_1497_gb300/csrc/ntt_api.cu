@@ -504,6 +504,19 @@ ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, voi
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "conv (scratch)");
 }
 
+// The exact convolution's fused launch for one prime (32-bit words, whole
+// sequences): see Launch::conv_exact.
+ntt_status ntt_launch_exact(ntt_plan_t p, bool garner, const void *f64, const void *g64, void *h, const void *exact_args,
+                            long long np, cudaStream_t st)
+{
+    if (!p || p->word != 32 || p->split) return ntt_fail(NTT_ERR_ARG, "exact fused launch: not a whole-sequence 32-bit plan");
+    RowArgs<uint32_t> a{(const uint32_t *)f64, (const uint32_t *)g64, (uint32_t *)h, nullptr, np, 0,
+                        (const uint32_t *)p->tw, p->c32};
+    const int grid = row_grid(p->nsm, np, Launch<uint32_t>::pairs_per_block(p->L));
+    cudaError_t e = Launch<uint32_t>::conv_exact(p->L, garner, a, *(const ntt::ExactArgs *)exact_args, grid, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "exact fused launch");
+}
+
 // Longest length a batch plan folds into its persistent launch: the
 // one-warp lengths by default (their bodies share one kernel without
 // spilling); NTT_PERSIST_LMAX raises it to every whole-sequence length.

@@ -17,54 +17,27 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
 #include "../../include/ntt_gb300.h"
 #include "ntt_internal.h"
 #include "nt_host.h"
+#include "ntt_exact.cuh"
 
 namespace {
 
 constexpr int KMAX = NTT_EXACT_MAX_PRIMES;
 typedef unsigned __int128 u128;
 typedef __int128 i128;
-
-// Residue and reconstruction constants of one prime, passed by value.
-struct PrimeC {
-    uint64_t m;
-    uint64_t onep;        // floor(2^64 / m): Shoup quotient of the factor 1
-    uint64_t r64;         // 2^64 mod m
-    int word;             // 32 or 64
-    int pad;
-};
-
-struct ExactArgs {
-    int k;                          // number of primes
-    int vec;                        // 1: every base is 16-byte aligned (four-element path)
-    long long n;                    // elements
-    PrimeC p[KMAX];
-    uint64_t inv[KMAX][KMAX];       // inv[i][j] = m_i^-1 mod m_j (i < j)
-    uint64_t invp[KMAX][KMAX];      // floor(inv 2^64 / m_j)
-    unsigned long long half_lo, half_hi;   // (M - 1) / 2
-    unsigned long long M_lo, M_hi;         // M
-};
-
-__device__ __forceinline__ uint64_t shoup64(uint64_t b, uint64_t z, uint64_t zp, uint64_t m)
-{
-    return b * z - __umul64hi(b, zp) * m;           // in [0, 2m) for any b < 2^64
-}
-
-__device__ __forceinline__ uint64_t csub64(uint64_t v, uint64_t m) { return v >= m ? v - m : v; }
-
-// <x>_m for a signed 64-bit x: reduce its two's-complement bits, then take
-// away 2^64 mod m when x is negative.
-__device__ __forceinline__ uint64_t residue(long long x, const PrimeC &p)
-{
-    uint64_t r = csub64(shoup64((uint64_t)x, 1, p.onep, p.m), p.m);
-    if (x < 0) r = r >= p.r64 ? r - p.r64 : r + p.m - p.r64;
-    return r;
-}
+using ntt::ExactArgs;
+using ntt::PrimeC;
+using ntt::csub64;
+using ntt::garner;
+using ntt::load_res;
+using ntt::residue;
+using ntt::shoup64;
 
 // Four elements per thread (16-byte loads and stores), f and g in one
 // launch; a scalar loop takes the tail and unaligned bases.
@@ -130,42 +103,7 @@ __global__ void k_exact_residues(const __grid_constant__ ExactArgs a, const long
     }
 }
 
-// Garner's mixed-radix reconstruction of one output from its residues.
-__device__ __forceinline__ long long garner(const ExactArgs &a, const uint64_t (&r)[KMAX])
-{
-    const u128 half = ((u128)a.half_hi << 64) | a.half_lo;
-    const u128 M = ((u128)a.M_hi << 64) | a.M_lo;
-    uint64_t v[KMAX];
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-        if (j >= a.k) break;
-        const PrimeC &pj = a.p[j];
-        uint64_t t = r[j];
-        // mixed-radix digit: t = (...((r_j - v_0) c_0j - v_1) c_1j ...) mod m_j
-#pragma unroll
-        for (int q = 0; q < KMAX; ++q) {
-            if (q >= j) break;
-            const uint64_t vq = csub64(shoup64(v[q], 1, pj.onep, pj.m), pj.m);     // v_q mod m_j
-            const uint64_t d = t >= vq ? t - vq : t + pj.m - vq;
-            t = csub64(shoup64(d, a.inv[q][j], a.invp[q][j], pj.m), pj.m);
-        }
-        v[j] = t;
-    }
-    // X = v_0 + m_0 (v_1 + m_1 (v_2 + ...)), Horner from the top digit
-    u128 X = 0;
-#pragma unroll
-    for (int j = KMAX - 1; j >= 0; --j)
-        if (j < a.k) X = X * a.p[j].m + v[j];
-    const i128 s = X > half ? (i128)X - (i128)M : (i128)X;
-    return (long long)s;
-}
-
-__device__ __forceinline__ uint64_t load_res(const ExactArgs &a, void *const *res, int j, long long i)
-{
-    return a.p[j].word == 32 ? (uint64_t) static_cast<const uint32_t *>(res[j])[i] : static_cast<const uint64_t *>(res[j])[i];
-}
-
-__global__ void k_exact_garner(const __grid_constant__ ExactArgs a, void *const *res, long long *__restrict__ h)
+__global__ void k_exact_garner(const __grid_constant__ ExactArgs a, const void *const *res, long long *__restrict__ h)
 {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -236,6 +174,7 @@ struct ntt_exact_s {
     void **ptrs_g = nullptr;          // ptrs_f + KMAX
     void *host_ptrs[2 * KMAX] = {};   // the same pointers, host side
     int nsm = 0;
+    bool fused = false;               // whole sequences, 32-bit primes: residues and Garner fused into the convolutions
 };
 
 extern "C" void ntt_exact_destroy(ntt_exact_t e)
@@ -324,6 +263,13 @@ extern "C" ntt_status ntt_exact_plan(uint32_t N, uint32_t bound_bits, ntt_exact_
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
+    e->fused = true;
+    for (int i = 0; i < e->k; ++i) {
+        ntt_plan_info_t info;
+        ntt_plan_get_info(e->plans[i], &info);
+        if (info.word_bits != 32 || info.four_step) e->fused = false;
+    }
+    if (const char *env = getenv("NTT_EXACT_FUSED")) e->fused = e->fused && atoi(env) != 0;
     *out = e;
     return NTT_OK;
 }
@@ -360,6 +306,20 @@ extern "C" ntt_status conv_exact(ntt_exact_t e, const int64_t *f, const int64_t 
         long long *hw = (long long *)h + off;
         // scratch bases are 256-byte aligned and hold whole waves, so only the
         // caller's bases decide the four-element path
+        if (e->fused) {
+            // one fused launch per prime: int64 inputs reduced in registers;
+            // the last prime reconstructs h from the others' residues
+            for (int i = 0; i < e->k; ++i) {
+                a.j = i;
+                a.h64 = hw;
+                for (int q = 0; q < KMAX; ++q) a.prev[q] = e->host_ptrs[q];
+                const bool last = i == e->k - 1;
+                ntt_status s = ntt_launch_exact(e->plans[i], last, fw, gw, last ? nullptr : e->host_ptrs[i], &a,
+                                                (long long)np, st);
+                if (s != NTT_OK) return s;
+            }
+            continue;
+        }
         a.vec = ((((uintptr_t)fw | (uintptr_t)gw | (uintptr_t)hw) & 15u) == 0) ? 1 : 0;
         k_exact_residues<<<grid, threads, 0, st>>>(a, fw, gw, e->ptrs_f, e->ptrs_g);
         cudaError_t err = cudaGetLastError();

@@ -28,5 +28,9 @@ bool ntt_tuned_schedule(int word_bits, int log2N, uint32_t *wave, int *twist);
 ntt_status ntt_launch_persistent(int word_bits, const void *descs, const void *items, int nitems, int *counter,
                                  const ntt_plan_t *plans, int lmax, int grid, size_t smem, cudaStream_t st);   // plans: indexed by log2 N, null where absent
 size_t ntt_full_smem(int word_bits, int log2N);
-int ntt_persist_lmax(int word_bits);   // longest length a batch plan runs in its persistent launch
+int ntt_persist_lmax(int word_bits);
+// the exact convolution's fused launch of one prime (32-bit plans of whole
+// sequences); exact_args: an ntt::ExactArgs
+ntt_status ntt_launch_exact(ntt_plan_t p, bool garner, const void *f64, const void *g64, void *h, const void *exact_args,
+                            long long np, cudaStream_t st);   // longest length a batch plan runs in its persistent launch
 int ntt_num_sms();

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "ntt_core.cuh"
+#include "ntt_exact.cuh"
 
 namespace ntt {
 
@@ -56,6 +57,49 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
 }
 
+// Input and output of the fused bodies: plain words (the default), or the
+// ends of the exact convolution fused in -- signed 64-bit inputs reduced
+// modulo the launch's prime (IN64), and for the last prime the Chinese
+// remainder reconstruction of each output from the earlier primes'
+// residues (GARNER), written as a signed 64-bit integer.
+struct NoExact { static constexpr bool IN64 = false, GARNER = false; };
+struct ExactResidues { static constexpr bool IN64 = true, GARNER = false; };
+struct ExactGarner { static constexpr bool IN64 = true, GARNER = true; };
+
+// Element i of a sequence whose first element is at base.
+template <class X, typename W>
+__device__ __forceinline__ W ld_elem(const W *base, uint32_t i, const ExactArgs *xa)
+{
+    if constexpr (X::IN64) return (W)residue(reinterpret_cast<const long long *>(base)[i], xa->p[xa->j]);
+    else return base[i];
+}
+
+// Sequence `pair` of a contiguous batch of words (or of signed 64-bit words).
+template <class X, typename W>
+__device__ __forceinline__ const W *seq_base(const W *batch, long long pair, uint32_t N)
+{
+    if constexpr (X::IN64) return reinterpret_cast<const W *>(reinterpret_cast<const long long *>(batch) + (size_t)pair * N);
+    else return batch + (size_t)pair * N;
+}
+
+// Canonical output r at index idx of sequence `pair` (hp: that sequence's words).
+template <class X, typename W>
+__device__ __forceinline__ void st_out(W *hp, long long pair, uint32_t N, uint32_t idx, W r, const ExactArgs *xa)
+{
+    if constexpr (X::GARNER) {
+        const size_t at = (size_t)pair * N + idx;
+        uint64_t rr[XKMAX];
+#pragma unroll
+        for (int q = 0; q < XKMAX; ++q) {
+            if (q >= xa->k) break;
+            rr[q] = q == xa->j ? (uint64_t)r : load_res(*xa, xa->prev, q, (long long)at);
+        }
+        xa->h64[at] = garner(*xa, rr);
+    } else {
+        hp[idx] = r;
+    }
+}
+
 // Fused convolution of whole sequences (L <= LR_max), persistent.  The block
 // stages the twiddle table in shared memory once.  Per pair, f and g are
 // transformed together (one set of twiddle reads serves both) through shared
@@ -64,8 +108,9 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 // At the start of each pair one thread asks the copy engine to bring the
 // next pair's f and g into L2, so their loads do not wait on HBM.
 // Rows [base + group, a.nrows) by steps of stride.
-template <typename W, int L, int SRC>
-__device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long base, long long stride)
+template <typename W, int L, int SRC, class X = NoExact>
+__device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long base, long long stride,
+                                                const ExactArgs *xa = nullptr)
 {
     using G = Geo<W, L>;
     constexpr int T = G::T, R = G::R, GPC = RowShape<W, L, L>::GPC;
@@ -87,9 +132,11 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
             const DevDesc<W> d = a.descs[pair];
             fp = d.f; gp = d.g; hp = d.h;
         } else {
-            fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
+            fp = seq_base<X>(a.f, pair, N); gp = seq_base<X>(a.g, pair, N);
+            hp = X::GARNER ? nullptr : a.h + (size_t)pair * N;
         }
     };
+    constexpr uint32_t INB = X::IN64 ? 8u : (uint32_t)sizeof(W);     // bytes per input element
     for (long long rho = base + gid; rho < a.nrows; rho += stride) {
         const W *fp, *gp;
         W *hp;
@@ -98,14 +145,14 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
             const W *fn, *gn;
             W *hn;
             ptrs(rho + stride, fn, gn, hn);
-            prefetch_l2(fn, N * (uint32_t)sizeof(W));
-            prefetch_l2(gn, N * (uint32_t)sizeof(W));
+            prefetch_l2(fn, N * INB);
+            prefetch_l2(gn, N * INB);
         }
         W v[2][R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            v[0][k] = fp[b0 + ((uint32_t)k << lo0)];
-            v[1][k] = gp[b0 + ((uint32_t)k << lo0)];
+            v[0][k] = ld_elem<X>(fp, b0 + ((uint32_t)k << lo0), xa);
+            v[1][k] = ld_elem<X>(gp, b0 + ((uint32_t)k << lo0), xa);
         }
         fwd_all<W, L, L, 0, 2, TW_SMEM, true>(v, 0u, tau, S, gid, stw, a.c);
 #pragma unroll
@@ -114,7 +161,7 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const uint32_t x = b0 + ((uint32_t)k << lo0);
-            hp[(N - x) & (N - 1u)] = canon<W>(v[0][k], (W)1, a.c.onep, a.c.m);
+            st_out<X>(hp, a.pair0 + rho, N, (N - x) & (N - 1u), canon<W>(v[0][k], (W)1, a.c.onep, a.c.m), xa);
         }
     }
 }
@@ -298,8 +345,9 @@ struct CRShape {
 // Rows [base + row group, end) by steps of stride; end is a.nrows unless ITEM.
 // OUT 0: canonical at <-x>_N (a whole convolution); OUT 1: lazy residues in
 // natural order (a row of a convolution's split path, after the twist).
-template <typename W, int L, int LROW, int SRC, bool ITEM = false, int OUT = 0>
-__device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long stride, long long end = 0)
+template <typename W, int L, int LROW, int SRC, bool ITEM = false, int OUT = 0, class X = NoExact>
+__device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long stride, long long end = 0,
+                                             const ExactArgs *xa = nullptr)
 {
     using SH = CRShape<W, L, LROW>;
     using GR = typename SH::GR;
@@ -337,7 +385,8 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
                 const DevDesc<W> d = a.descs[pair];
                 fp = d.f; gp = d.g; hp = d.h;
             } else {
-                fp = a.f + (size_t)pair * N; gp = a.g + (size_t)pair * N; hp = a.h + (size_t)pair * N;
+                fp = seq_base<X>(a.f, pair, N); gp = seq_base<X>(a.g, pair, N);
+                hp = X::GARNER ? nullptr : a.h + (size_t)pair * N;
             }
             rowoff = 0;
         } else {
@@ -357,8 +406,9 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
 #pragma unroll
-            for (int k = 0; k < RC; ++k) dst[j * RC + k] = src[ptau + (uint32_t)j * TPP + ((uint32_t)k << RW)];
+            for (int k = 0; k < RC; ++k) dst[j * RC + k] = ld_elem<X>(src, ptau + (uint32_t)j * TPP + ((uint32_t)k << RW), xa);
     };
+    constexpr uint32_t INB = X::IN64 ? 8u : (uint32_t)sizeof(W);     // bytes per input element
     long long rho = base + pid;
     W v[2][R];
     const W *fp = nullptr, *gp = nullptr;
@@ -384,8 +434,8 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
             W *hn;
             uint32_t ro;
             ptrs(rho + stride, fn, gn, hn, ro);
-            prefetch_l2(fn, (1u << LROW) * (uint32_t)sizeof(W));
-            prefetch_l2(gn, (1u << LROW) * (uint32_t)sizeof(W));
+            prefetch_l2(fn, (1u << LROW) * INB);
+            prefetch_l2(gn, (1u << LROW) * INB);
         }
         // forward, column phase: columns c = ptau + j TPP, elements x = c + k 2^RW
         // (f's columns go to shared memory while g's levels run: measured
@@ -445,7 +495,8 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const uint32_t x = ptau + (uint32_t)j * TPP + ((uint32_t)k << RW);
-                if constexpr (FULL && OUT == 0) hcur[(N - x) & (N - 1u)] = canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m);
+                if constexpr (FULL && OUT == 0)
+                    st_out<X>(hcur, a.pair0 + rho, N, (N - x) & (N - 1u), canon<W>(v[0][j * RC + k], (W)1, a.c.onep, a.c.m), xa);
                 else hcur[x] = v[0][j * RC + k];
             }
     }
@@ -456,6 +507,23 @@ __global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(const __grid_constant__ Ro
 {
     constexpr int PPC = CRShape<W, L, LROW>::PPC;
     conv_cr_body<W, L, LROW, SRC, false, OUT>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC);
+}
+
+// The exact convolution's fused launches (whole sequences, contiguous):
+// X = ExactResidues for every prime but the last (its residues of h go to
+// a.h), X = ExactGarner for the last (h goes to e.h64 as signed integers).
+template <typename W, int L, class X>
+__global__ void __launch_bounds__(BLOCK, 1) k_conv_exact(const __grid_constant__ RowArgs<W> a,
+                                                          const __grid_constant__ ExactArgs e)
+{
+    constexpr int RW = Arith<W>::RB + 5;
+    if constexpr (L <= RW) {
+        constexpr int GPC = RowShape<W, L, L>::GPC;
+        conv_fused_body<W, L, 0, X>(a, (long long)blockIdx.x * GPC, (long long)gridDim.x * GPC, &e);
+    } else {
+        constexpr int PPC = CRShape<W, L, L>::PPC;
+        conv_cr_body<W, L, L, 0, false, 0, X>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC, 0, &e);
+    }
 }
 
 // ---- one persistent launch for every whole-sequence length of a batch ----

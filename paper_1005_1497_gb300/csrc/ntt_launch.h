@@ -32,6 +32,10 @@ template <typename W> struct Launch {
                              const ModC<W> &c, int grid, cudaStream_t st);
     static cudaError_t check_range(const W *data, long long n, W m, unsigned long long *bad, int grid,
                                    cudaStream_t st);
+    // the exact convolution's fused launch of one prime (whole sequences,
+    // contiguous, signed 64-bit inputs): residues of h to a.h, or (garner)
+    // the reconstructed signed 64-bit h to e.h64
+    static cudaError_t conv_exact(int L, bool garner, const RowArgs<W> &a, const ExactArgs &e, int grid, cudaStream_t st);
     // dynamic shared memory of the whole-sequence fused kernel of length 2^L
     static size_t conv_full_smem(int L);
     // one persistent launch over a work list of whole-sequence items

@@ -131,3 +131,27 @@ def test_conv_exact_unaligned_buffers(ntt, orc):
     for b in range(batch):
         assert np.array_equal(hv[b].cpu().numpy(), orc.int_conv(f[b], g[b]))
     plan.close()
+
+
+@pytest.mark.parametrize("N,bound", [(1, 20), (64, 44), (1024, 60), (4096, 44), (1 << 14, 40)])
+def test_conv_exact_fused_equals_three_passes(ntt, orc, monkeypatch, N, bound):
+    """The fused launches (int64 inputs reduced in registers, Garner in the
+    last prime's epilogue) and the three-pass form give the same words."""
+    amp = amp_for(N, bound)
+    batch = 4
+    f, g = signed_inputs(batch, N, amp, seed=N + 7)
+    fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    outs = []
+    for fused in ("1", "0"):
+        monkeypatch.setenv("NTT_EXACT_FUSED", fused)
+        plan = ntt.ExactPlan(N, bound)
+        outs.append(ntt.conv_exact(plan, fd, gd).cpu())
+        plan.close()
+    assert torch.equal(outs[0], outs[1])
+    h = outs[0].numpy()
+    for b in range(batch):
+        if N <= 4096:
+            assert np.array_equal(h[b], orc.int_conv(f[b], g[b]))
+        else:
+            idx = np.random.default_rng(b).integers(0, N, 32, dtype=np.uint64)
+            assert np.array_equal(h[b][idx.astype(np.int64)], orc.int_conv_sample(f[b], g[b], idx))
