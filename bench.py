@@ -353,6 +353,28 @@ def run_ours(args):
                                      "tuned_ms": round(tuned["ms"], 4), "heuristic_ms": round(tuned["default_ms"], 4)}
 
     if not args.quick:
+        # standalone natural-order transforms of the same batch (Eq. 2 and 3):
+        # 8 algorithmic bytes per element (read x, write X)
+        X = torch.empty_like(f)
+        tsteps = max(1, min(args.steps // 4, 200))
+        ntt_rates = {}
+        for name, fn in (("forward", ntt.ntt_forward), ("inverse", ntt.ntt_inverse)):
+            for _ in range(3):
+                fn(plan, f, out=X, stream=stream)
+            torch.cuda.synchronize()
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            for _ in range(tsteps):
+                fn(plan, f, out=X, stream=stream)
+            t1e.record(stream)
+            torch.cuda.synchronize()
+            tms = max_over_ranks(world, t0e.elapsed_time(t1e) / tsteps)
+            gbps = 8.0 * N * batch / (tms * 1e-3) / 1e9
+            ntt_rates[name] = {"ms": round(tms, 4), "GBps": round(gbps, 1), "frac_hbm": round(gbps / hbm_peak, 4),
+                               "transforms_per_s": round(batch * world * 1000.0 / tms, 1)}
+        out["ntt"] = ntt_rates
+        del X
+
         # plain form: one launch per butterfly stage over the whole batch
         work = torch.empty((2 * batch, N), dtype=torch.int32, device="cuda")
         h2 = torch.empty_like(f)
