@@ -211,7 +211,11 @@ static cudaError_t launch_ntt_full(const NttArgs<W> &a, int grid, cudaStream_t s
 template <typename W, int L, bool INV>
 static cudaError_t launch_bitrev(const W *src, W *dst, long long batch, const ModC<W> &c, cudaStream_t st)
 {
-    if constexpr (L >= 1) {
+    if constexpr (L >= 10) {
+        const long long tiles = batch << (L - 10);
+        k_bitrev_tiled<W, L, INV><<<(unsigned)tiles, 256, 0, st>>>(src, dst, batch, c);
+        return cudaGetLastError();
+    } else if constexpr (L >= 1) {
         const long long n = batch << L;
         k_bitrev_out<W, L, INV><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, batch, c);
         return cudaGetLastError();

@@ -925,6 +925,47 @@ __global__ void k_bitrev_out(const W *__restrict__ src, W *__restrict__ dst, lon
     dst[idx] = csub<W>(shoup<W>(src[(size_t)b * N + x], scale, scalep, c.m), c.m);
 }
 
+// The same gather, tiled (L >= 10): write an index as (h, m, l) with h and
+// l of 5 bits, so brv(h, m, l) = (brv l, brv m, brv h).  For one value of m
+// the 32 x 32 elements u = (uh, m, ul) come from x = (brv ul, brv m, brv uh):
+// a block reads them as 32 contiguous source runs (fixed brv ul), passes
+// them through a padded shared tile, and writes 32 contiguous destination
+// runs (fixed uh) -- both directions coalesced.  INV writes u to <-u>_N,
+// which keeps every destination run contiguous (descending).
+template <typename W, int L, bool INV>
+__global__ void __launch_bounds__(256) k_bitrev_tiled(const W *__restrict__ src, W *__restrict__ dst, long long batch,
+                                                     ModC<W> c)
+{
+    static_assert(L >= 10, "two 5-bit ends");
+    constexpr uint32_t N = 1u << L;
+    constexpr int LM = L - 10;                         // middle bits
+    __shared__ W tile[32][33];
+    const long long t = blockIdx.x;                    // (sequence, m)
+    const long long b = t >> LM;
+    const uint32_t m = (uint32_t)t & ((1u << LM) - 1u);
+    const uint32_t mb = LM ? (__brev(m) >> (32 - LM)) : 0u;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const W *s = src + (size_t)b * N;
+    W *d = dst + (size_t)b * N;
+    const W scale = INV ? c.ninv : (W)1;
+    const W scalep = INV ? c.ninvp : c.onep;
+    // source runs: x = (sh, mb, sl), sh = brv(ul) fixed per run, sl = lane
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t sh = wid * 4 + r;
+        tile[sh][lane] = s[(sh << (L - 5)) | (mb << 5) | lane];
+    }
+    __syncthreads();
+    // destination runs: u = (uh, m, ul), ul = lane; value at x = (brv ul, mb, brv uh)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t uh = wid * 4 + r;
+        const uint32_t u = (uh << (L - 5)) | (m << 5) | lane;
+        const W v = tile[__brev(lane) >> 27][__brev(uh) >> 27];
+        d[INV ? ((N - u) & (N - 1u)) : u] = csub<W>(shoup<W>(v, scale, scalep, c.m), c.m);
+    }
+}
+
 // ---------------------------------------------------- plain per-stage form
 
 // One forward tree level over the whole batch of f and g: work = [2][batch][N].
