@@ -197,14 +197,7 @@ static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
 template <typename W, int L, bool INV>
 static cudaError_t launch_ntt_full(const NttArgs<W> &a, int grid, cudaStream_t st)
 {
-    constexpr int RW = Arith<W>::RB + 5;
-    if constexpr (L > RW && L <= LRMax<W>::v) {            // column/row form
-        constexpr size_t smem = CRShape<W, L, L>::smem;
-        static const cudaError_t init = ensure_smem(k_ntt_cr<W, L, INV>, smem);
-        if (init != cudaSuccess) return init;
-        k_ntt_cr<W, L, INV><<<grid, BLOCK, smem, st>>>(a);
-        return cudaGetLastError();
-    } else if constexpr (L <= LRMax<W>::v) {
+    if constexpr (L <= LRMax<W>::v) {
         constexpr size_t smem = TwBytes<W, L>::v + RowShape<W, L, L>::smem(1);
         static const cudaError_t init = ensure_smem(k_ntt_rows<W, L, INV>, smem);
         if (init != cudaSuccess) return init;

@@ -647,80 +647,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(const __grid_constant__ N
     }
 }
 
-// The same transforms for 2^RW < N <= 2^LR_max in the column/row form of
-// the convolution kernel: column levels in registers, one block transpose,
-// the row levels warp by warp (warp wr owns the elements x = wr 2^RW + y),
-// then one shared-memory pass that puts X(brv_L(x)) at u = brv_L(x) (or
-// <-u>_N with N^-1 for the inverse) and stores natural order, coalesced.
-template <typename W, int L, bool INV>
-__global__ void __launch_bounds__(BLOCK, 1) k_ntt_cr(const __grid_constant__ NttArgs<W> a)
-{
-    using SH = CRShape<W, L, L>;
-    using GR = typename SH::GR;
-    constexpr int RW = SH::RW, LC = SH::LC, RC = SH::RC, TPP = SH::TPP, PPC = SH::PPC, CPT = SH::CPT;
-    constexpr int R = GR::R;
-    static_assert(LC >= 1 && CPT * RC == R, "column/row split");
-    constexpr uint32_t N = 1u << L;
-    constexpr int last = GR::NPASS - 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int pid = threadIdx.x / TPP;
-    const uint32_t ptau = threadIdx.x % TPP;
-    const int wr = (int)(ptau >> 5);
-    const uint32_t lane = ptau & 31u;
-    W *stw = reinterpret_cast<W *>(smem_raw);
-    W *P = reinterpret_cast<W *>(smem_raw + TwBytes<W, L>::v) + (size_t)pid * RC * 2 * GR::ROWP;
-    W *Srow = P + (size_t)wr * 2 * GR::ROWP;
-    const uint32_t b0 = GR::base(0, lane), bl = GR::base(last, lane);
-    constexpr int lo0 = GR::lo(0), lol = GR::lo(last);
-    stage_twiddles<W>(a.tw, stw, TwBytes<W, L>::pairs);
-    __syncthreads();
-    auto psync = [&]() {
-        if constexpr (TPP == BLOCK) __syncthreads();
-        else asm volatile("bar.sync %0, %1;" ::"r"(pid + 1), "r"(TPP) : "memory");
-    };
-    const W scale = INV ? a.c.ninv : (W)1;
-    const W scalep = INV ? a.c.ninvp : a.c.onep;
-    const uint32_t wbrv = __brev((uint32_t)wr) >> (32 - LC);          // brv_LC(wr)
-
-    for (long long rho = (long long)blockIdx.x * PPC + pid; rho < a.batch; rho += (long long)gridDim.x * PPC) {
-        const W *xp = a.x + (size_t)rho * N;
-        W *yp = a.y + (size_t)rho * N;
-        W v[1][R];
-        // column levels: columns c = ptau + j TPP, elements x = c + k 2^RW
-#pragma unroll
-        for (int j = 0; j < CPT; ++j)
-#pragma unroll
-            for (int k = 0; k < RC; ++k) v[0][j * RC + k] = xp[ptau + (uint32_t)j * TPP + ((uint32_t)k << RW)];
-        colf_all<W, LC, 0, CPT, 0, TW_SMEM, R>(v[0], 0u, stw, a.c);
-        psync();                                            // region free (previous sequence)
-#pragma unroll
-        for (int j = 0; j < CPT; ++j)
-#pragma unroll
-            for (int k = 0; k < RC; ++k)
-                P[(size_t)k * 2 * GR::ROWP + GR::pad(ptau + (uint32_t)j * TPP)] = v[0][j * RC + k];
-        psync();
-        // row levels (warp wr, row wr)
-#pragma unroll
-        for (int k = 0; k < R; ++k) v[0][k] = Srow[GR::pad(b0 + ((uint32_t)k << lo0))];
-        fwd_all<W, L, RW, 0, 1, TW_SMEM>(v, (uint32_t)wr << RW, lane, Srow, 0, stw, a.c);
-        psync();                                            // every row done with its slice
-        // X(brv_L(x)) to u = brv_L(x) = brv_RW(y) 2^LC + brv_LC(wr), y the row position
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const uint32_t y = bl + ((uint32_t)k << lol);
-            const uint32_t u = ((__brev(y) >> (32 - RW)) << LC) | wbrv;
-            P[GR::pad(u)] = v[0][k];
-        }
-        psync();
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const uint32_t u = ptau + (uint32_t)i * TPP;
-            const W val = csub<W>(shoup<W>(P[GR::pad(u)], scale, scalep, a.c.m), a.c.m);
-            yp[INV ? ((N - u) & (N - 1u)) : u] = val;
-        }
-    }
-}
-
 // Split path for L > LR: "column" transforms of the top LC = L - LR index
 // bits.  Element (c, k) of a sequence is x = c + k 2^LR (c < 2^LR, k < 2^LC);
 // every level of the top bits has node index k >> (bits below), the same for
