@@ -119,8 +119,9 @@ def test_conv_u64(ntt, orc, L):
     assert np.array_equal(h, ref_conv(orc, f, g, M64, plan.omega))
 
 
-@pytest.mark.parametrize("m,L", [(641, 6), (2424833, 10), (M, 1), (M, 7), (M, 11), (M, 14), (M, 15), (M, 19),
-                                 (M64, 9), (M64, 14), (M64, 19), (M64, 20)])
+@pytest.mark.parametrize("m,L", [(641, 6), (2424833, 10), (319489, 12), (M, 1), (M, 7), (M, 10), (M, 11), (M, 12),
+                                 (M, 13), (M, 14), (M, 15), (M, 19), (M64, 9), (M64, 10), (M64, 13), (M64, 14),
+                                 (M64, 19), (M64, 20)])
 def test_ntt_forward_inverse(ntt, orc, m, L):
     N = 1 << L
     plan = ntt.Plan(m, N)
