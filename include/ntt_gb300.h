@@ -78,12 +78,17 @@ const char *ntt_last_error(void);
 /* ------------------------------------------------------------------ plans */
 
 /* Create a plan for length N modulo m (Eq. 2/3 with w = 2^(ord_m(2)/N),
- * Sec. I; multiplicative inverse of N by extended Euclid, Appendix A).
- * Validates that m is prime and that ord_m(2) is a power of two (Prop. 2),
- * and that N is a power of two dividing ord_m(2) (Sec. I).  Supported
- * lengths: 1 <= N <= 2^19 for 32-bit words, 1 <= N <= 2^18 for 64-bit
- * words.  Builds the twiddle table {2^e mod m} on the host by doubling and
- * uploads it once to the current device; it stays resident.  Synchronous.
+ * Sec. I; the multiplicative inverse of N mod m (Appendix A) as N^(m-2),
+ * m prime).  Validates that m is prime and that ord_m(2) is a power of two
+ * (Prop. 2), and that N is a power of two dividing ord_m(2) (Sec. I).
+ * Supported lengths: 1 <= N <= 2^20 (the largest order of 2 among the
+ * supported primes is 2^19 for 32-bit words and 2^20 for 64-bit words).
+ * Builds the twiddle table {2^e mod m} on the host by doubling and uploads it
+ * once to the current device; it stays resident.  Synchronous.
+ * Lengths above one thread block (2^14 for 32-bit words, 2^13 for 64-bit)
+ * use the plan's scratch: calls with such a plan must not overlap on the GPU
+ * (issue them on one stream, or use one plan per stream); other plans have
+ * no such restriction.
  * Errors: NTT_ERR_MODULUS, NTT_ERR_LENGTH, NTT_ERR_WORD, NTT_ERR_OOM,
  * NTT_ERR_CUDA, NTT_ERR_ARG (out == NULL). */
 ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out);
