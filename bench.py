@@ -173,7 +173,8 @@ def shard_pairs(total: int, world: int, rank: int) -> tuple[int, int]:
 
 def traffic_from_profile(kernel_tag: str):
     """DRAM bytes per launch recorded by an ncu capture summary in profiles/, if
-    it was taken on the current kernel sources (digest line matches)."""
+    it was taken on the current kernel code (its kernel_digest line matches:
+    the kernel-defining sources without comments, and the compile flags)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
         return None
@@ -184,7 +185,7 @@ def traffic_from_profile(kernel_tag: str):
             if ":" in line:
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("sources_digest") != build.sources_digest():
+    if vals.get("kernel_digest") != build.kernel_digest():
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

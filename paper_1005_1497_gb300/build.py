@@ -89,6 +89,31 @@ def _prune(keep) -> None:
 
 
 
+_KERNEL_SOURCES = ("csrc/ntt_core.cuh", "csrc/ntt_kernels.cuh", "csrc/ntt_exact.cuh", "csrc/launch_impl.cuh",
+                   "csrc/ntt_launch.h", "../include/ntt_gb300.h")
+
+
+def _strip_comments(text: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_digest(root: str | None = None) -> str:
+    """Digest of the code that defines the kernels (comments and layout
+    ignored) and of the compile flags: a profile taken with the same digest
+    measured the same kernels.  ``root`` reads the sources of another
+    checkout (default: this one)."""
+    base = os.path.join(root, "paper_1005_1497_gb300") if root else HERE
+    h = hashlib.sha256(" ".join(ARCH + FLAGS[:-2]).encode())
+    for rel in _KERNEL_SOURCES:
+        with open(os.path.normpath(os.path.join(base, rel)), encoding="utf-8") as fh:
+            h.update(rel.encode() + _strip_comments(fh.read()).encode())
+    return h.hexdigest()[:16]
+
+
 def sources_digest() -> str:
     """Digest of every CUDA source and header plus the flags: identifies the
     kernels a profile summary was captured on."""
