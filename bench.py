@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--workload", default="conv2", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="fused timing only (no plain form, e2e, CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--log2n", type=int, default=None,
+                    help="override log2 N of the uniform workloads (conv1/conv2/conv3 shapes), e.g. for profiling")
+    ap.add_argument("--batch", type=int, default=None, help="override the number of pairs of the uniform workloads")
     ap.add_argument("--schedule", default=None,
                     help="split-path schedule file: loaded if it exists (no autotuning), else written after tuning")
     return ap.parse_args()
@@ -251,6 +254,10 @@ def run_ours(args):
     if args.workload == "shift7":
         return run_shift(args, world, rank, local)
     batch, L, desc = WORKLOADS[args.workload]
+    if args.log2n is not None or args.batch is not None:
+        L = args.log2n if args.log2n is not None else L
+        batch = args.batch if args.batch is not None else batch
+        desc = f"uniform batch: {batch} pairs x N=2^{L}, m=13631489, uint32 (override)"
     N = 1 << L
     tuned = None
     if L > 14:                                                    # split path: pick form and pairs per wave
