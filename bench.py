@@ -238,6 +238,16 @@ def cpu_oracle_rate(f, g, m: int, budget_s: float, threads: int | None = None):
 
 # ---------------------------------------------------------------- our path
 
+def count_launches(ntt, fn) -> int:
+    """Kernel launches one call of fn issues, by the library's own counter
+    (an untimed call, before the warm-up)."""
+    import torch
+    c0 = ntt.launch_count()
+    fn()
+    torch.cuda.synchronize()
+    return ntt.launch_count() - c0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -274,10 +284,11 @@ def run_ours(args):
     g = inputs.uniform_mod_torch(M, batch * N, seed, 1, device="cuda").view(batch, N)
     h = torch.empty_like(f)
     stream = torch.cuda.current_stream()
-    launches_per_step = 1 if not plan.four_step else 3 * -(-batch // plan.wave)
 
     def step():
         ntt.conv_circular(plan, f, g, out=h, stream=stream)
+
+    launches_per_step = count_launches(ntt, step)
 
     # A launch-bound step (one small convolution) is replayed from a CUDA
     # graph captured once, so that the host's per-call cost is not timed as
@@ -492,6 +503,7 @@ def run_shift(args, world, rank, local):
                        "main_fused_path": {"value": rate(ms_main), "ms_per_step": round(ms_main, 4),
                                            "bit_identical": same_main}},
            "clocks": clk.summary(), "gpu_launches": steps}
+    attach_cpu_baseline(out, args, world, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -515,11 +527,11 @@ def run_exact(args, world, rank, local):
     g = inputs.uniform_mod_torch(2 * amp + 1, batch * N, seed, 1, device="cuda", dtype=torch.int64).view(batch, N) - amp
     h = torch.empty_like(f)
     stream = torch.cuda.current_stream()
-    waves = -(-batch // plan.wave)
-    launches_per_step = waves * (3 + len(plan.primes))     # 2 residue passes, one conv per prime, reconstruction
 
     def step():
         ntt.conv_exact(plan, f, g, out=h, stream=stream)
+
+    launches_per_step = count_launches(ntt, step)         # per wave: residues, one conv per prime, reconstruction
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -653,11 +665,13 @@ def run_uneven(args, world, rank, local):
     steps = max(1, min(args.steps, 200))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        c0 = ntt.launch_count()
         e0.record(stream)
         for _ in range(steps):
             bp.exec_graph(stream)
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = ntt.launch_count() - c0
     ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
     hbm_peak, sm_max_mhz, peak_src = peaks()
     alg_bytes = 12.0 * total
@@ -677,7 +691,8 @@ def run_uneven(args, world, rank, local):
            "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / (ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
                             "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                             "peak_src": f"{peak_src} copy bandwidth"},
-           "clocks": clk.summary()}
+           "clocks": clk.summary(), "gpu_launches": launches}
+    attach_cpu_baseline(out, args, world, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -713,6 +728,7 @@ def run_serve(args, world, rank, local):
     srv.reset_stats()
     ids = [0] * count
     with ClockSampler(local) as clk:
+        c0 = ntt.launch_count()
         t0 = time.perf_counter()
         for i in range(count):
             target = t0 + arrivals[i]
@@ -724,6 +740,7 @@ def run_serve(args, world, rank, local):
             st, ids[i] = srv.submit_raw(fp + 8 * offs[s], gp + 8 * offs[s], hp + 8 * offs[s], int(lens[s]))
         srv.drain()
         elapsed = time.perf_counter() - t0
+        launches = ntt.launch_count() - c0
     stats = srv.stats()
     # capacity: the same requests submitted back to back (closed loop, K in flight)
     srv.reset_stats()
@@ -754,12 +771,114 @@ def run_serve(args, world, rank, local):
            "capacity": {"req_per_s": round(cap["completed"] / cap_elapsed, 1), "requests": ccount,
                         "in_flight": K, "p50_us": round(cap["p50_us"], 1), "p99_us": round(cap["p99_us"], 1),
                         "GBps_host_io": round(24.0 * mean_n * cap["completed"] / cap_elapsed / 1e9, 1)},
-           "clocks": clk.summary()}
+           "clocks": clk.summary(), "gpu_launches": launches}
+    attach_cpu_baseline(out, args, world, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------------- reference arm
+
+def oracle_rate_mixed(pairs, budget_s: float):
+    """Time the oracle on sampled outputs of a list of pairs (f, g, m, kind):
+    kind "mod" is Eq. 1 modulo m (or_conv_sample), "int" the exact integer
+    convolution (or_int_conv_sample).  Every host thread takes blocks of
+    output indices round-robin over the pairs (8 on the first visit of a pair,
+    256 after), so that each pair is sampled however mixed the lengths; a
+    pair's time is its sampled seconds scaled by N / outputs (each output of
+    the oracle costs N products), and the rate is threads x pairs over the sum
+    of those times.  Returns (conv/s, threads, outputs, wall s)."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle()
+    threads = os.cpu_count() or 1
+    P = len(pairs)
+    stop = time.perf_counter() + budget_s
+    lock = threading.Lock()
+    nxt = [0]
+    cursor, spent, outs = [0] * P, [0.0] * P, [0] * P
+
+    def worker():
+        while True:
+            with lock:
+                k = nxt[0]
+                if k >= P and time.perf_counter() >= stop:
+                    return
+                nxt[0] += 1
+                i = k % P
+                f, g, m, kind = pairs[i]
+                N = f.shape[-1]
+                cnt = min(N, 8 if k < P else 256)
+                off = cursor[i]
+                cursor[i] = (off + cnt) % N
+            idx = ((off + np.arange(cnt, dtype=np.uint64)) % np.uint64(N)).astype(np.uint64)
+            t = time.perf_counter()
+            if kind == "int":
+                o.int_conv_sample(f, g, idx)
+            else:
+                o.conv_sample(f, g, m, idx)
+            dt = time.perf_counter() - t
+            with lock:
+                spent[i] += dt
+                outs[i] += cnt
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    el = time.perf_counter() - t0
+    est = sum(spent[i] * pairs[i][0].shape[-1] / outs[i] for i in range(P))
+    return threads * P / est, threads, sum(outs), el
+
+
+def reference_pairs(args):
+    """Up to 64 pairs of the workload, from the same seeded generators."""
+    import numpy as np
+
+    from paper_1005_1497_gb300 import inputs
+    w = args.workload
+    if w == "conv4":
+        lens = inputs.log_uniform_lengths(WORKLOADS["conv4"][0], 6, 19, seed=1000)[:64]
+        return [(*(a[0] for a in inputs.pairs(M, 1, int(n), seed=1000 + i)), M, "mod")
+                for i, n in enumerate(lens)], WORKLOADS[w][2], "conv/s"
+    if w == "serve5":
+        m64 = 70525124609
+        lens = inputs.log_uniform_lengths(512, 8, 18, seed=2000)[:64]
+        return [(*(a[0] for a in inputs.pairs(m64, 1, int(n), seed=2000 + i)), m64, "mod")
+                for i, n in enumerate(lens)], WORKLOADS[w][2], "req/s"
+    batch, L, desc = WORKLOADS[w]
+    if args.log2n is not None:
+        L = args.log2n
+    N = 1 << L
+    if w == "exact6":
+        amp = 1 << 15
+        out = []
+        for i in range(min(batch, 64)):
+            f = inputs.uniform_mod(2 * amp + 1, N, 1000 + i, 0, dtype=np.uint64).astype(np.int64) - amp
+            g = inputs.uniform_mod(2 * amp + 1, N, 1000 + i, 1, dtype=np.uint64).astype(np.int64) - amp
+            out.append((f, g, 0, "int"))
+        return out, desc, "conv/s"
+    m = 641 if w == "shift7" else M
+    f, g = inputs.pairs(m, min(batch, 64), N, seed=1000)
+    return [(f[i], g[i], m, "mod") for i in range(f.shape[0])], desc, "conv/s"
+
+
+def attach_cpu_baseline(out, args, world, rank):
+    """The oracle's rate on the workload's own pairs (every length of a mixed
+    workload sampled), rank 0 at N=1 only, within --cpu-seconds."""
+    if world != 1 or rank != 0:
+        return
+    pairs, _, unit = reference_pairs(args)
+    rate, thr, done, el = oracle_rate_mixed(pairs, args.cpu_seconds)
+    kind = "exact integer Eq. 1 (oracle or_int_conv_sample)" if pairs[0][3] == "int" else \
+        "direct Eq. 1 (oracle or_conv_sample)"
+    out["cpu_baseline"] = {"value": round(rate, 4), "unit": unit, "cores": thr, "kind": "oracle",
+                           "sample": f"{kind} on {done} output indices sampled from each of {len(pairs)} pairs of "
+                                     f"the workload in {el:.1f} s; each pair's time scaled to all N outputs"}
+
 
 def run_reference(args):
     """The oracle, as it stands, timed on the host cores on bounded samples of
@@ -767,28 +886,26 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_1005_1497_gb300 import inputs
-    batch, L, desc = WORKLOADS[args.workload]
-    N = 1 << L
-    f, g = inputs.pairs(M, min(batch, 64), N, seed=1000)
+    pairs, desc, unit = reference_pairs(args)
     per_step = max(1.0, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_oracle_rate(f, g, M, per_step / 4)
-    rates, total_done, total_el, thr = [], 0, 0.0, 1
+        oracle_rate_mixed(pairs, per_step / 4)
+    rates, total_out, thr = [], 0, 1
     for _ in range(args.steps):
-        r, thr, done, el = cpu_oracle_rate(f, g, M, per_step)
+        r, thr, done, _ = oracle_rate_mixed(pairs, per_step)
         rates.append(r)
-        total_done += done
-        total_el += el
-    value = total_done / N / total_el
-    sample = f"direct Eq. 1 on {total_done} output indices of the first {f.shape[0]} pairs, {per_step:.1f} s per step"
-    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "conv/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / value * batch, 1),
+        total_out += done
+    value = statistics.median(rates)
+    kind = "exact integer Eq. 1 in 128-bit integers" if pairs[0][3] == "int" else "direct Eq. 1"
+    sample = (f"{kind} on {total_out} output indices sampled from each of {len(pairs)} pairs of the workload, "
+              f"{per_step:.1f} s per step; each pair's time scaled from its sampled outputs to all N of them")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": unit, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 * per_step, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (oracle, __int128 products)",
-           "data": "synthetic (seeded counter-based uniform residues in [0,m))",
-           "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "m": M, "form": "CPU oracle"},
-           "cpu_baseline": {"value": round(value, 4), "unit": "conv/s", "cores": thr, "kind": "oracle", "sample": sample},
-           "e2e": {"value": round(value, 4), "unit": "conv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "data": "synthetic (seeded counter-based)",
+           "config": {"workload": desc, "form": "CPU oracle", "pairs_sampled": len(pairs)},
+           "cpu_baseline": {"value": round(value, 4), "unit": unit, "cores": thr, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 

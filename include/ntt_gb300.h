@@ -75,6 +75,14 @@ const char *ntt_status_str(ntt_status s);
  * thread, overwritten by the next failure; "" if none). */
 const char *ntt_last_error(void);
 
+/* Kernel launches the library has issued in this process, counted on the
+ * host as each launch is enqueued (all threads, all devices).  A replay by
+ * ntt_batch_exec_graph counts the kernel nodes of its graph; launches that
+ * a caller records into its own stream capture count once, at capture, and
+ * replays of that graph are not seen.  The difference across a call is the
+ * number of GPU kernels the call ran.  Never fails; needs no GPU. */
+uint64_t ntt_launch_count(void);
+
 /* ------------------------------------------------------------------ plans */
 
 /* Create a plan for length N modulo m (Eq. 2/3 with w = 2^(ord_m(2)/N),

@@ -32,13 +32,13 @@ static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t 
         static const cudaError_t init = ensure_smem(k_conv_fused<W, L, SRC>, smem);
         if (init != cudaSuccess) return init;
         k_conv_fused<W, L, SRC><<<grid, BLOCK, smem, st>>>(a);
-        return cudaGetLastError();
+        return launched();
     } else if constexpr (L <= LRMax<W>::v) {
         constexpr size_t smem = CRShape<W, L>::smem;
         static const cudaError_t init = ensure_smem(k_conv_cr<W, L, L, SRC>, smem);
         if (init != cudaSuccess) return init;
         k_conv_cr<W, L, L, SRC><<<grid, BLOCK, smem, st>>>(a);
-        return cudaGetLastError();
+        return launched();
     } else {
         return cudaErrorInvalidValue;
     }
@@ -74,7 +74,7 @@ static cudaError_t launch_persistent(const PersistArgs<W> &a, int grid, size_t s
     }();
     if (init != cudaSuccess) return init;
     k_conv_persistent<W, HI><<<grid, BLOCK, smem, st>>>(a);
-    return cudaGetLastError();
+    return launched();
 }
 
 template <typename W>
@@ -93,7 +93,7 @@ static cudaError_t launch_exact(const RowArgs<W> &a, const ExactArgs &e, int gri
         static const cudaError_t init = ensure_smem(k_conv_exact<W, L, X>, smem);
         if (init != cudaSuccess) return init;
         k_conv_exact<W, L, X><<<grid, BLOCK, smem, st>>>(a, e);
-        return cudaGetLastError();
+        return launched();
     } else {
         return cudaErrorInvalidValue;
     }
@@ -128,7 +128,7 @@ static cudaError_t launch_conv_rows(bool twisted, const RowArgs<W> &a, int grid,
             if (init != cudaSuccess) return init;
             k_conv_cr<W, L, LR, 0><<<grid, BLOCK, smem, st>>>(a);
         }
-        return cudaGetLastError();
+        return launched();
     } else {
         return cudaErrorInvalidValue;
     }
@@ -143,7 +143,7 @@ static cudaError_t launch_rows_fwd(const RowArgs<W> &a, int grid, cudaStream_t s
         static const cudaError_t init = ensure_smem(k_rows_fwd<W, L, LR>, smem);
         if (init != cudaSuccess) return init;
         k_rows_fwd<W, L, LR><<<grid, BLOCK, smem, st>>>(a);
-        return cudaGetLastError();
+        return launched();
     } else {
         return cudaErrorInvalidValue;
     }
@@ -171,7 +171,7 @@ static cudaError_t launch_cols_fwd(const ColArgs<W> &a, cudaStream_t st)
             const long long t2 = a.npairs << (L - CS::LB);
             k_cols_mid_fwd<W, L, CS::LR, CS::LB, NS, TW><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
         }
-        return cudaGetLastError();
+        return launched(CS::TWO ? 2 : 1);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -188,7 +188,7 @@ static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
         }
         const long long threads = a.npairs << CS::TOPLR;
         k_cols_inv<W, L, CS::TOPLR, DST, TW && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
-        return cudaGetLastError();
+        return launched(CS::TWO ? 2 : 1);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -202,7 +202,7 @@ static cudaError_t launch_ntt_full(const NttArgs<W> &a, int grid, cudaStream_t s
         static const cudaError_t init = ensure_smem(k_ntt_rows<W, L, INV>, smem);
         if (init != cudaSuccess) return init;
         k_ntt_rows<W, L, INV><<<grid, BLOCK, smem, st>>>(a);
-        return cudaGetLastError();
+        return launched();
     } else {
         return cudaErrorInvalidValue;
     }
@@ -214,11 +214,11 @@ static cudaError_t launch_bitrev(const W *src, W *dst, long long batch, const Mo
     if constexpr (L >= 10) {
         const long long tiles = batch << (L - 10);
         k_bitrev_tiled<W, L, INV><<<(unsigned)tiles, 256, 0, st>>>(src, dst, batch, c);
-        return cudaGetLastError();
+        return launched();
     } else if constexpr (L >= 1) {
         const long long n = batch << L;
         k_bitrev_out<W, L, INV><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, batch, c);
-        return cudaGetLastError();
+        return launched();
     } else {
         return cudaErrorInvalidValue;
     }
@@ -366,14 +366,14 @@ cudaError_t Launch<W>::plain(int L, const W *f, const W *g, W *h, W *work, long 
     } else {
         for (int d = 0; d < L; ++d) {
             k_plain_fwd<W><<<grid, threads, 0, st>>>(f, g, work, batch, L, d, tw, c);
-            cudaError_t e = cudaGetLastError();
+            cudaError_t e = launched();
             if (e != cudaSuccess) return e;
         }
     }
     k_plain_pointwise<W><<<grid, threads, 0, st>>>(work, batch, L, c);
     for (int d = L - 1; d >= 0; --d) k_plain_inv<W><<<grid, threads, 0, st>>>(work, batch, L, d, tw, c);
     k_plain_final<W><<<grid, threads, 0, st>>>(work, h, batch, L, c);
-    return cudaGetLastError();
+    return launched(L + 2);
 }
 
 template <typename W>
@@ -381,7 +381,7 @@ cudaError_t Launch<W>::check_range(const W *data, long long n, W m, unsigned lon
                                    cudaStream_t st)
 {
     k_check_range<W><<<grid, 256, 0, st>>>(data, n, m, bad);
-    return cudaGetLastError();
+    return launched();
 }
 
 }  // namespace ntt

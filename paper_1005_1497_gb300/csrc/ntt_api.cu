@@ -69,6 +69,12 @@ extern "C" const char *ntt_status_str(ntt_status s)
 
 extern "C" const char *ntt_last_error(void) { return g_last_error; }
 
+namespace ntt {
+std::atomic<unsigned long long> launch_count{0};
+}
+
+extern "C" uint64_t ntt_launch_count(void) { return ntt::launch_count.load(std::memory_order_relaxed); }
+
 // ------------------------------------------------------------------- plans
 
 struct ntt_plan_s {

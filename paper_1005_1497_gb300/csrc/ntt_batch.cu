@@ -15,6 +15,7 @@
 
 #include "../../include/ntt_gb300.h"
 #include "ntt_internal.h"
+#include "ntt_count.h"
 #include "ntt_launch.h"
 
 
@@ -72,6 +73,7 @@ struct ntt_batch_s {
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    unsigned kernel_nodes = 0;       // kernel launches one replay of gexec runs
     std::vector<ntt_conv_desc> host_descs;   // copy, for cache comparison
 };
 
@@ -247,9 +249,22 @@ extern "C" ntt_status ntt_batch_exec_graph(ntt_batch_t b, ntt_stream_t stream)
         b->graph = g;
         if (cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess)
             return ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec_graph: instantiate");
+        // the captured launches were counted as issued but did not run:
+        // take them back, and count the graph's kernel nodes per replay
+        size_t n = 0;
+        cudaGraphGetNodes(g, nullptr, &n);
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (n) cudaGraphGetNodes(g, nodes.data(), &n);
+        for (size_t i = 0; i < n; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->kernel_nodes;
+        }
+        ntt::launch_count.fetch_sub(b->kernel_nodes, std::memory_order_relaxed);
     }
     cudaError_t e = cudaGraphLaunch(b->gexec, user);
-    return e == cudaSuccess ? NTT_OK : ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec_graph: launch: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec_graph: launch: %s", cudaGetErrorString(e));
+    ntt::launch_count.fetch_add(b->kernel_nodes, std::memory_order_relaxed);
+    return NTT_OK;
 }
 
 extern "C" ntt_status conv_batched(uint64_t m, const ntt_conv_desc *descs, size_t count, ntt_stream_t stream)

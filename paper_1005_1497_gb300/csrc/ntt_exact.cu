@@ -24,6 +24,7 @@
 #include "../../include/ntt_gb300.h"
 #include "ntt_internal.h"
 #include "nt_host.h"
+#include "ntt_count.h"
 #include "ntt_exact.cuh"
 
 namespace {
@@ -327,14 +328,14 @@ extern "C" ntt_status conv_exact(ntt_exact_t e, const int64_t *f, const int64_t 
         }
         a.vec = ((((uintptr_t)fw | (uintptr_t)gw | (uintptr_t)hw) & 15u) == 0) ? 1 : 0;
         k_exact_residues<<<grid, threads, 0, st>>>(a, fw, gw, e->ptrs_f, e->ptrs_g);
-        cudaError_t err = cudaGetLastError();
+        cudaError_t err = ntt::launched();
         if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: residues: %s", cudaGetErrorString(err));
         for (int i = 0; i < e->k; ++i) {
             ntt_status s = conv_circular(e->plans[i], e->host_ptrs[i], e->host_ptrs[KMAX + i], e->host_ptrs[i], np, stream);
             if (s != NTT_OK) return s;
         }
         k_exact_garner<<<grid, threads, 0, st>>>(a, e->ptrs_f, hw);
-        err = cudaGetLastError();
+        err = ntt::launched();
         if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: reconstruction: %s", cudaGetErrorString(err));
     }
     return NTT_OK;

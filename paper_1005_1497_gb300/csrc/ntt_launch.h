@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include "ntt_count.h"
 #include "ntt_kernels.cuh"
 
 namespace ntt {

@@ -28,6 +28,7 @@
 #include <cstring>
 
 #include "../../include/ntt_gb300.h"
+#include "ntt_count.h"
 #include "ntt_internal.h"
 #include "nt_host.h"
 
@@ -215,7 +216,7 @@ template <int K, bool SHIFT>
 cudaError_t launch(int L, const ShiftArgs &a, int grid, cudaStream_t st)
 {
     switch (L) {
-#define C(X) case X: if constexpr ((2 * K >> X) >= 1) { k_conv_shift<K, X, SHIFT><<<grid, BLK, 0, st>>>(a); return cudaGetLastError(); } break;
+#define C(X) case X: if constexpr ((2 * K >> X) >= 1) { k_conv_shift<K, X, SHIFT><<<grid, BLK, 0, st>>>(a); return ntt::launched(); } break;
     C(1) C(2) C(3) C(4) C(5) C(6)
 #undef C
     default: break;

@@ -26,6 +26,7 @@ _VP, _U64, _U32, _SZ, _INT = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, 
 SIGNATURES = {
     "ntt_status_str": (ctypes.c_char_p, [_INT]),
     "ntt_last_error": (ctypes.c_char_p, []),
+    "ntt_launch_count": (_U64, []),
     "ntt_plan": (_INT, [_U64, _U32, ctypes.POINTER(_VP)]),
     "ntt_plan_destroy": (None, [_VP]),
     "ntt_plan_get_info": (_INT, [_VP, _VP]),
@@ -107,6 +108,12 @@ def lib():
 def _check(status: int, where: str):
     if status != NTT_OK:
         raise NttError(status, where, lib().ntt_last_error().decode(errors="replace"))
+
+
+def launch_count() -> int:
+    """``ntt_launch_count()``: kernel launches the library has issued in this
+    process (a batch plan's graph replay counts its kernel nodes)."""
+    return int(lib().ntt_launch_count())
 
 
 def _stream(stream) -> ctypes.c_void_p:

@@ -123,3 +123,9 @@ def test_exact_candidate_primes_are_fermat_factors(orc):
 def test_shift_rejects(ntt, m, N, mode, status):
     buf = ctypes.c_void_p(16)   # never dereferenced: validation fails first
     assert ntt.lib().conv_circular_shift(m, N, buf, buf, buf, 1, mode, None) == status
+
+
+def test_launch_counter_needs_no_gpu(ntt):
+    a = ntt.launch_count()
+    assert isinstance(a, int) and a >= 0
+    assert ntt.launch_count() >= a
