@@ -692,6 +692,29 @@ def run_uneven(args, world, rank, local):
                             "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                             "peak_src": f"{peak_src} copy bandwidth"},
            "clocks": clk.summary(), "gpu_launches": launches}
+    # end to end: each step copies f and g in from pinned host memory (one
+    # copy each), replays the batch plan and copies h back
+    h_dev = h.clone()
+    fh, gh = f.cpu().pin_memory(), g.cpu().pin_memory()
+    hh = torch.empty_like(fh).pin_memory()
+    esteps = max(1, min(args.steps, 5))
+    for i in range(esteps + 1):
+        if i == 1:
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+        f.copy_(fh, non_blocking=True)
+        g.copy_(gh, non_blocking=True)
+        bp.exec_graph(stream)
+        hh.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    ems = max_over_ranks(world, (time.perf_counter() - t0) * 1000.0 / esteps)
+    out["e2e"] = {"value": round(count * world * 1000.0 / ems, 1), "unit": "conv/s", "ms_per_step": round(ems, 3),
+                  "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 4 * total,
+                  "entry": "ntt_batch_exec_graph between one host-to-device copy of f and of g (pinned) and one "
+                           "device-to-host copy of h",
+                  "bit_identical_to_device_path": bool(torch.equal(hh, h_dev.cpu()))}
+    bp.close()
     attach_cpu_baseline(out, args, world, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -772,6 +795,12 @@ def run_serve(args, world, rank, local):
                         "in_flight": K, "p50_us": round(cap["p50_us"], 1), "p99_us": round(cap["p99_us"], 1),
                         "GBps_host_io": round(24.0 * mean_n * cap["completed"] / cap_elapsed / 1e9, 1)},
            "clocks": clk.summary(), "gpu_launches": launches}
+    # the serving rate is itself end to end: every request goes from host
+    # memory to its result in host memory through ntt_server_submit
+    out["e2e"] = {"value": out["value"], "unit": "req/s", "h2d_bytes_per_step": round(16.0 * mean_n, 1),
+                  "d2h_bytes_per_step": round(8.0 * mean_n, 1),
+                  "entry": "ntt_server_submit / ntt_server_wait on pinned host buffers (a step is one request; "
+                           "mean bytes read and written across the host link)"}
     attach_cpu_baseline(out, args, world, rank)
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -204,7 +204,7 @@ void ntt_batch_destroy(ntt_batch_t batch);
 
 typedef struct {
     uint32_t wave;          /* chosen pairs per scratch wave (split path) */
-    uint32_t default_wave;  /* the heuristic choice (4 rows per SM per wave) */
+    uint32_t default_wave;  /* the heuristic choice (4 rows per SM, or 256 MB of scratch if more) */
     uint32_t twist;         /* chosen form: 1 the four-step twist, 0 row-dependent twiddles */
     uint32_t default_twist; /* the heuristic form */
     double ms;              /* time of one convolution call over `batch` pairs with the choice */

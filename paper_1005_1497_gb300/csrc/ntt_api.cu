@@ -92,6 +92,7 @@ struct ntt_plan_s {
     bool twist = false;                // split path form: the four-step twist (else row-dependent twiddles)
     void *scratch = nullptr;           // 2 * wave * N words
     void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
+    void *pd = nullptr;                // one column pass: the twist factor of element x, at x (the diagonal)
     void *pwl = nullptr;               // split path: (w^(s l), quotient) at s 32 + l, s < 2^(L - LR), l < 32
     int nsm = 1;
     int device = 0;
@@ -132,6 +133,7 @@ extern "C" void ntt_plan_destroy(ntt_plan_t p)
     cudaFree(p->tw);
     cudaFree(p->scratch);
     cudaFree(p->pw);
+    cudaFree(p->pd);
     cudaFree(p->pwl);
     cudaFree(p->counter);
     cudaFree(p->stage);
@@ -196,18 +198,22 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
     else fill_modc(p->c64, m, p->n_inv);
 
     if (p->split) {
-        // Enough pairs per wave to fill every SM with rows several times over,
-        // while the scratch (2 N words per pair) stays a few tens of MB.
+        // Pairs per wave: at least enough to fill every SM with rows several
+        // times over, and as many as 256 MB of scratch (2 N words per pair)
+        // holds -- fewer, longer launches; the autotuner chose such waves on
+        // GB300 (64 pairs of 2^19 words, the whole of the uneven batch's
+        // classes), where the scratch is a small part of the 280 GB.
         const uint64_t rows_per_pair = 1ull << (L - p->LR);
         uint32_t tuned_wave = 0;
         int tuned_twist = -1;
         ntt_tuned_schedule(word, L, &tuned_wave, &tuned_twist);      // autotuned schedule, if any
         uint64_t wave = tuned_wave;
-        if (wave == 0) wave = (uint64_t)p->nsm * 4 / rows_per_pair;
-        // Form: the twist wins for 64-bit words and for few column bits
-        // (measured on GB300: u64 2^16 -23%, u64 2^18 -15%, u32 2^15 -4%,
-        // u32 2^19 +19%); the autotuner measures both.
-        p->twist = tuned_twist >= 0 ? tuned_twist != 0 : (word == 64 || L - p->LR <= 2);
+        if (wave == 0)
+            wave = std::max<uint64_t>((uint64_t)p->nsm * 4 / rows_per_pair, (256ull << 20) / (2 * (uint64_t)N * elt));
+        // Form: the twist, measured faster on GB300 at every length (u64 2^16
+        // -23%, 2^18 -15%; u32 2^19 -1%, and the autotuner's choice for every
+        // u32 class 2^15..2^19); the autotuner measures both.
+        p->twist = tuned_twist >= 0 ? tuned_twist != 0 : true;
         if (const char *env = getenv("NTT_SPLIT_TWIST")) p->twist = atoi(env) != 0;   // explicit override
         if (wave < 1) wave = 1;
         p->wave = (uint32_t)wave;
@@ -228,6 +234,22 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         }
         if (cudaMalloc(&p->pw, tab.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: power table");
         CUDA_TRY(cudaMemcpy(p->pw, tab.data(), tab.size(), cudaMemcpyHostToDevice), "ntt_plan: upload powers");
+        if (L - p->LR <= 5) {
+            // one column pass: element x = t + k 2^LR (t < 2^LR, k < 2^(L-LR))
+            // takes w^(brv(k) t), the same for every pair, so the factor is
+            // stored at x and read in the data's own (coalesced) layout
+            const int lc = L - p->LR;
+            std::vector<unsigned char> dg(tab.size());
+            for (size_t x = 0; x < N; ++x) {
+                const size_t k = x >> p->LR, t = x & (((size_t)1 << p->LR) - 1);
+                size_t sk = 0;
+                for (int i = 0; i < lc; ++i) sk |= ((k >> i) & 1u) << (lc - 1 - i);
+                const size_t e = (sk * t) % N;
+                memcpy(&dg[2 * x * elt], &tab[2 * e * elt], 2 * elt);
+            }
+            if (cudaMalloc(&p->pd, dg.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twist diagonal");
+            CUDA_TRY(cudaMemcpy(p->pd, dg.data(), dg.size(), cudaMemcpyHostToDevice), "ntt_plan: upload twist diagonal");
+        }
         const size_t ns = (size_t)1 << (L - p->LR);
         std::vector<unsigned char> lt(2 * ns * 32 * elt);
         for (size_t sidx = 0; sidx < ns; ++sidx)
@@ -295,7 +317,7 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     for (long long w0 = 0; w0 < batch; w0 += wave) {
         const long long np = std::min<long long>(wave, batch - w0);
         ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c, (const W *)p->pw,
-                      (const W *)p->pwl};
+                      (const W *)p->pwl, (const W *)p->pd};
         cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, tw_form, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);

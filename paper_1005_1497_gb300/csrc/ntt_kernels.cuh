@@ -669,6 +669,7 @@ template <typename W> struct ColArgs {
     ModC<W> c;
     const W *pw;        // convolutions: (w^e, Shoup quotient) pairs, e < N (the twist)
     const W *pwl;       // (w^(s l), quotient) at s 32 + l, s < 2^(L-LR), l < 32
+    const W *pd;        // one column pass: (w^(brv(k) t), quotient) at x = t + k 2^LR
 };
 
 // The four-step twist, one of the two forms of a convolution's split path
@@ -683,18 +684,49 @@ template <typename W> struct ColArgs {
 // kernel.  The inverse (the transposed tree) applies the same diagonal
 // between the rows and the transposed column levels.  Output in [0, 2m).
 //
-// The factor is split as w^(s t0) w^(s l) with t = t0 + l, l = t mod 32 (the
-// lane): the first is the same for a warp (one broadcast load), the second
-// comes from a small lane-contiguous table (a coalesced load); two Shoup
-// products, in kernels bound by HBM.
+// With one column pass the factor of element x = t + k 2^LR depends on x
+// alone (not on the pair), so the plan stores it at x (ColArgs::pd): one
+// coalesced, L2-resident vector load and one Shoup product per element.
+// With two column passes (k_cols_mid_*) it is split as w^(s t0) w^(s l),
+// t = t0 + l, l = t mod 32 (the lane): the first is the same for a warp (one
+// broadcast load), the second comes from a small lane table (s, l) ->
+// w^(s l), coalesced; two Shoup products.  Each (power, Shoup quotient)
+// pair is one vector load.
+template <typename W> struct PairVec;
+template <> struct PairVec<uint32_t> { using T = uint2; };
+template <> struct PairVec<uint64_t> { using T = ulonglong2; };
+
+template <typename W>
+__device__ __forceinline__ void ld_pair_g(const W *p, W &z, W &zp)
+{
+    const typename PairVec<W>::T q = __ldg(reinterpret_cast<const typename PairVec<W>::T *>(p));
+    z = q.x; zp = q.y;
+}
+
+template <typename W>
+__device__ __forceinline__ void ld_pair(const W *p, W &z, W &zp)
+{
+    const typename PairVec<W>::T q = *reinterpret_cast<const typename PairVec<W>::T *>(p);
+    z = q.x; zp = q.y;
+}
+
+// The twist factor of (s, t): e = s (t - l) mod N for the warp-uniform part;
+// lt is the lane table (shared memory, or the plan's copy).
 template <typename W, int L>
-__device__ __forceinline__ W twist(W v, uint32_t s, uint32_t t, const ColArgs<W> &a)
+__device__ __forceinline__ void twist_factors(uint32_t s, uint32_t t, const ColArgs<W> &a, const W *lt, W &z0, W &z0p,
+                                              W &z1, W &z1p)
 {
     const uint32_t l = t & 31u;
     const uint32_t e = (s * (t - l)) & ((1u << L) - 1u);
-    const W z0 = __ldg(a.pw + 2 * (size_t)e), z0p = __ldg(a.pw + 2 * (size_t)e + 1);
-    const size_t i = (size_t)s * 32 + l;
-    const W z1 = __ldg(a.pwl + 2 * i), z1p = __ldg(a.pwl + 2 * i + 1);
+    ld_pair_g<W>(a.pw + 2 * (size_t)e, z0, z0p);
+    ld_pair<W>(lt + 2 * ((size_t)s * 32 + l), z1, z1p);
+}
+
+template <typename W, int L>
+__device__ __forceinline__ W twist(W v, uint32_t s, uint32_t t, const ColArgs<W> &a, const W *lt)
+{
+    W z0, z0p, z1, z1p;
+    twist_factors<W, L>(s, t, a, lt, z0, z0p, z1, z1p);
     return shoup<W>(shoup<W>(v, z1, z1p, a.c.m), z0, z0p, a.c.m);
 }
 
@@ -760,15 +792,40 @@ __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArg
     if (idx >= a.npairs << LR) return;
     const long long pw = idx >> LR;
     const uint32_t col = (uint32_t)idx & ((1u << LR) - 1u);
-#pragma unroll 1
-    for (int s = 0; s < NS; ++s) {
-        const W *src;
+    auto source = [&](int s) -> const W * {
         if constexpr (SRC == 1) {
             const DevDesc<W> d = a.descs[a.pair0 + pw];
-            src = s == 0 ? d.f : d.g;
+            return s == 0 ? d.f : d.g;
         } else {
-            src = (s == 0 ? a.src0 : a.src1) + (size_t)(a.pair0 + pw) * N;
+            return (s == 0 ? a.src0 : a.src1) + (size_t)(a.pair0 + pw) * N;
         }
+    };
+    if constexpr (TWIST && NS == 2 && sizeof(W) == 4) {
+        // 32-bit words: f and g together, so that each twist factor is
+        // loaded once for both
+        const W *sf = source(0), *sg = source(1);
+        W vf[RC], vg[RC];
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            vf[k] = sf[col + ((uint32_t)k << LR)];
+            vg[k] = sg[col + ((uint32_t)k << LR)];
+        }
+        col_fwd_levels<W, L, LR, L - LR - 1>(vf, a.tw, a.c);
+        col_fwd_levels<W, L, LR, L - LR - 1>(vg, a.tw, a.c);
+        W *df = a.dst0 + (size_t)pw * N, *dg = a.dst1 + (size_t)pw * N;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            const uint32_t x = col + ((uint32_t)k << LR);
+            W z, zp;
+            ld_pair_g<W>(a.pd + 2 * (size_t)x, z, zp);
+            df[x] = csub<W>(shoup<W>(vf[k], z, zp, a.c.m), a.c.m);
+            dg[x] = csub<W>(shoup<W>(vg[k], z, zp, a.c.m), a.c.m);
+        }
+        return;
+    }
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+        const W *src = source(s);
         W *dst = (s == 0 ? a.dst0 : a.dst1) + (size_t)pw * N;
         W v[RC];
 #pragma unroll
@@ -777,7 +834,9 @@ __global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArg
         if constexpr (TWIST) {
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
-                v[k] = csub<W>(twist<W, L>(v[k], brv_c32<L - LR>((uint32_t)k), col, a), a.c.m);
+                W z, zp;
+                ld_pair_g<W>(a.pd + 2 * (size_t)(col + ((uint32_t)k << LR)), z, zp);
+                v[k] = csub<W>(shoup<W>(v[k], z, zp, a.c.m), a.c.m);
                 // 64-bit words: keep the compiler from hoisting every table
                 // load ahead of the products (it spills them otherwise)
                 if constexpr (sizeof(W) == 8 && RC > 8)
@@ -812,7 +871,9 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
     if constexpr (TWIST) {
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
-            v[k] = twist<W, L>(v[k], brv_c32<LC>((uint32_t)k), col, a);
+            W z, zp;
+            ld_pair_g<W>(a.pd + 2 * (size_t)(col + ((uint32_t)k << LR)), z, zp);
+            v[k] = shoup<W>(v[k], z, zp, a.c.m);
             if constexpr (sizeof(W) == 8 && RC > 8)
                 if ((k & 7) == 7) asm volatile("" ::: "memory");
         }
@@ -854,7 +915,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_fwd(const __grid_constant__ Co
             const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
 #pragma unroll
             for (int k = 0; k < RC; ++k)
-                v[k] = csub<W>(twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a), a.c.m);
+                v[k] = csub<W>(twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a, a.pwl), a.c.m);
         }
 #pragma unroll
         for (int k = 0; k < RC; ++k) p[base + ((uint32_t)k << BLO)] = v[k];
@@ -880,7 +941,7 @@ __global__ void __launch_bounds__(256) k_cols_mid_inv(const __grid_constant__ Co
         const uint32_t hbrv = __brev(hi) >> (32 - (L - BLO - LB));
 #pragma unroll
         for (int k = 0; k < RC; ++k)
-            v[k] = twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a);
+            v[k] = twist<W, L>(v[k], (brv_c32<LB>((uint32_t)k) << (L - BLO - LB)) | hbrv, lo, a, a.pwl);
     }
     colg_levels<W, LB, 0, 0, L - BLO - LB, TW_GLOBAL, RC>(v, hi << LB, a.tw, a.c);
 #pragma unroll
