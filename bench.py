@@ -432,6 +432,36 @@ def run_ours(args):
                       "h2d_bytes_per_step": 2 * batch * N * 4, "d2h_bytes_per_step": batch * N * 4,
                       "entry": "conv_circular_host (pinned host buffers, chunked copy/compute overlap)",
                       "bit_identical_to_device_path": bool(torch.equal(hh, h.cpu()))}
+        # the host link alone, for the same bytes (plain copies, untimed
+        # above): f and g in, h out, and both directions at once -- the
+        # least time a step's copies can take
+        side = torch.cuda.Stream()
+
+        def copies_ms(h2d, d2h, reps=5):
+            def once():
+                if d2h:
+                    side.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.stream(side):
+                        hh.copy_(h, non_blocking=True)
+                if h2d:
+                    f.copy_(fh, non_blocking=True)
+                    g.copy_(gh, non_blocking=True)
+                if d2h:
+                    torch.cuda.current_stream().wait_stream(side)
+            once()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(reps):
+                once()
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t) * 1000.0 / reps
+
+        in_ms, out_ms, both_ms = copies_ms(True, False), copies_ms(False, True), copies_ms(True, True)
+        out["e2e"]["host_link"] = {"h2d_GBps": round(2 * batch * N * 4 / (in_ms * 1e-3) / 1e9, 1),
+                                   "d2h_GBps": round(batch * N * 4 / (out_ms * 1e-3) / 1e9, 1),
+                                   "both_directions_ms": round(both_ms, 3),
+                                   "frac": round(both_ms / ems, 4),
+                                   "note": "frac = the step's copies alone (both directions at once) / e2e step time"}
         if world == 1 and rank == 0:
             nb = min(batch, 64)
             f_np, g_np = fh[:nb].numpy().view(np.uint32), gh[:nb].numpy().view(np.uint32)

@@ -153,14 +153,19 @@ ntt_status conv_circular(ntt_plan_t plan, const void *f_dev, const void *g_dev, 
 ntt_status conv_circular_plain(ntt_plan_t plan, const void *f_dev, const void *g_dev, void *h_dev,
                                size_t batch, void *work_dev, ntt_stream_t stream);
 
-/* conv_circular with the inputs and output in HOST memory.  Page-locked
- * buffers (cudaHostAlloc / cudaHostRegister), which the GPU addresses over
- * the C2C link, are read and written in place by the kernels.  Otherwise the
- * library copies f and g to the device, convolves, and copies h back, in
- * chunks on `stream` so that the copies of one chunk overlap the
- * convolution of the next, with device staging memory allocated on first
- * use (kept by the plan).  Returns after h_host is complete (synchronises
- * `stream`).  Errors: NTT_ERR_ARG, NTT_ERR_OOM, NTT_ERR_CUDA. */
+/* conv_circular with the inputs and output in HOST memory (pageable or
+ * page-locked).  The library copies f and g to the device, convolves and
+ * copies h back in chunks of about 32 MB of input, ordered after `stream`'s
+ * earlier work, on three internal streams (inbound copies, convolutions,
+ * outbound copies) so that those steps of different chunks overlap.  Device
+ * staging memory (4 slots x 3 chunks, about 200 MB at most) is allocated on
+ * first use and kept by the plan.  With page-locked buffers (cudaHostAlloc /
+ * cudaHostRegister), which the GPU can address over the C2C link, the
+ * environment variable NTT_HOST_DIRECT=p (0..100) sends p percent of the
+ * pairs through the kernels in place instead, for whole-sequence lengths
+ * (default 0: measured slower than the copies).  Returns after h_host is
+ * complete (synchronises `stream`).  Errors: NTT_ERR_ARG, NTT_ERR_OOM,
+ * NTT_ERR_CUDA. */
 ntt_status conv_circular_host(ntt_plan_t plan, const void *f_host, const void *g_host, void *h_host,
                               size_t batch, ntt_stream_t stream);
 

@@ -783,8 +783,11 @@ __device__ __forceinline__ void col_fwd_levels(W (&v)[1 << (L - LR)], const W *_
     }
 }
 
+// (the twisted 32-bit form holds f and g at once: at most 80 registers keep
+// three blocks, 24 warps, on an SM for the loads in flight)
 template <typename W, int L, int LR, int NS, int SRC, bool TWIST>
-__global__ void __launch_bounds__(256) k_cols_fwd(const __grid_constant__ ColArgs<W> a)
+__global__ void __launch_bounds__(256, (TWIST && NS == 2 && sizeof(W) == 4) ? 3 : 1)
+    k_cols_fwd(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int RC = 1 << (L - LR);
     constexpr uint32_t N = 1u << L;

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import oracle
+from paper_1005_1497_gb300 import inputs
 from gpu_util import M, M64, TABLE1, dev, host, need_gpu, pairs
 
 pytestmark = pytest.mark.gpu
@@ -179,7 +180,6 @@ def test_in_place_and_deterministic(ntt, orc):
 
 
 def test_conv_batched_uneven(ntt, orc):
-    from paper_1005_1497_gb300 import inputs
     lens = inputs.log_uniform_lengths(60, 0, 19, seed=7)
     triples, ref = [], []
     for i, N in enumerate(lens):
@@ -216,7 +216,6 @@ def test_conv_batched_persistent(ntt, orc, monkeypatch, m, word, lmax):
     whose blocks pull work items from a counter: many short pairs of every
     length up to one block's, some computed in place (h = f), executed
     eagerly twice and by graph replay twice (the counter is re-armed)."""
-    from paper_1005_1497_gb300 import inputs
     if lmax is not None:
         monkeypatch.setenv("NTT_PERSIST_LMAX", str(lmax))
     top = 14 if word == 32 else 13
@@ -289,6 +288,28 @@ def test_host_buffers(ntt, orc, monkeypatch, direct):
         hp = torch.empty_like(ft)                                   # pageable output
         ntt.conv_circular_host(plan, ft.clone(), gt.clone(), hp)
         assert np.array_equal(hp.numpy().astype(np.uint64), want)
+
+
+def test_host_buffers_many_chunks(ntt, orc):
+    """More chunks than the host pipeline has slots (1100 pairs of 2^14:
+    four full chunks of 256 pairs and a ragged fifth), so slots are reused
+    within a call; identical to the device path, and the last pairs checked
+    against Eq. 1 on sampled outputs."""
+    N, batch = 1 << 14, 1100
+    plan = ntt.Plan(M, N)
+    ft = inputs.uniform_mod_torch(M, batch * N, 77, 0, device="cpu").view(batch, N).pin_memory()
+    gt = inputs.uniform_mod_torch(M, batch * N, 77, 1, device="cpu").view(batch, N).pin_memory()
+    ht = torch.empty_like(ft).pin_memory()
+    ntt.conv_circular_host(plan, ft, gt, ht)
+    ntt.conv_circular_host(plan, ft, gt, ht)                     # again: staging kept by the plan
+    want = ntt.conv_circular(plan, ft.cuda(), gt.cuda()).cpu()
+    assert torch.equal(ht, want)
+    rng = np.random.default_rng(5)
+    for b in (0, 255, 256, 1023, 1024, batch - 1):
+        idx = rng.integers(0, N, 16, dtype=np.uint64)
+        fb, gb = ft[b].numpy().astype(np.uint64), gt[b].numpy().astype(np.uint64)
+        got = ht[b].numpy().astype(np.uint64)[idx.astype(np.int64)]
+        assert np.array_equal(got, orc.conv_sample(fb, gb, M, idx)), b
 
 
 def test_autotune_schedule_roundtrip(ntt, orc, tmp_path):
