@@ -71,6 +71,107 @@ __device__ __forceinline__ void residues_scalar(const ExactArgs &a, const long l
     }
 }
 
+// Every prime below 2^25 (32-bit words, the usual case): a residue is two
+// 32-bit Shoup products, one per half of the input's bits, and for one or
+// two primes Garner's reconstruction fits 64-bit arithmetic (M < 2^50).
+// The residue arrays travel in the kernel parameters.
+struct Exact32 {
+    int k;
+    int pad;
+    long long n;                           // elements of this wave
+    uint32_t m[KMAX];
+    uint32_t c[KMAX], cp[KMAX];            // 2^32 mod m and its Shoup quotient
+    uint32_t onep[KMAX];                   // floor(2^32 / m): Shoup quotient of the factor 1
+    uint32_t r64[KMAX];                    // 2^64 mod m
+    uint32_t inv01, inv01p;                // m_0^-1 mod m_1 and its Shoup quotient (k == 2)
+    unsigned long long M, half;            // k <= 2: the product of the primes and (M - 1) / 2
+    uint32_t *rf[KMAX], *rg[KMAX];         // residues of f (the convolutions leave h's there) and of g
+};
+
+__device__ __forceinline__ uint32_t shoup32(uint32_t b, uint32_t z, uint32_t zp, uint32_t m)
+{
+    return b * z - __umulhi(b, zp) * m;     // in [0, 2m) for any b < 2^32
+}
+
+// <x>_m of a signed 64-bit x: its bits as hi 2^32 + lo, each half reduced by
+// a Shoup product (sum below 4m), then 2^64 mod m taken away if x < 0.
+__device__ __forceinline__ uint32_t residue32(long long x, const Exact32 &a, int j)
+{
+    const uint64_t u = (uint64_t)x;
+    const uint32_t lo = (uint32_t)u, hi = (uint32_t)(u >> 32), m = a.m[j];
+    uint32_t s = shoup32(hi, a.c[j], a.cp[j], m) + shoup32(lo, 1u, a.onep[j], m);
+    s = s >= 2 * m ? s - 2 * m : s;
+    s = s >= m ? s - m : s;
+    if (x < 0) s = s >= a.r64[j] ? s - a.r64[j] : s + m - a.r64[j];
+    return s;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_exact_residues32(const __grid_constant__ Exact32 a,
+                                                          const long long *__restrict__ f,
+                                                          const long long *__restrict__ g)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long n4 = a.n / 4;                       // bases are 16-byte aligned (checked by the caller)
+    for (long long q = tid; q < n4; q += nthr) {
+        const longlong2 f0 = __ldcs(reinterpret_cast<const longlong2 *>(f) + 2 * q);
+        const longlong2 f1 = __ldcs(reinterpret_cast<const longlong2 *>(f) + 2 * q + 1);
+        const longlong2 g0 = __ldcs(reinterpret_cast<const longlong2 *>(g) + 2 * q);
+        const longlong2 g1 = __ldcs(reinterpret_cast<const longlong2 *>(g) + 2 * q + 1);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            reinterpret_cast<uint4 *>(a.rf[j])[q] = make_uint4(residue32(f0.x, a, j), residue32(f0.y, a, j),
+                                                               residue32(f1.x, a, j), residue32(f1.y, a, j));
+            reinterpret_cast<uint4 *>(a.rg[j])[q] = make_uint4(residue32(g0.x, a, j), residue32(g0.y, a, j),
+                                                               residue32(g1.x, a, j), residue32(g1.y, a, j));
+        }
+    }
+    for (long long i = 4 * n4 + tid; i < a.n; i += nthr) {
+        const long long x = f[i], y = g[i];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            a.rf[j][i] = residue32(x, a, j);
+            a.rg[j][i] = residue32(y, a, j);
+        }
+    }
+}
+
+// Garner for one or two 32-bit primes: v_0 = r_0, v_1 = (r_1 - v_0) m_0^-1
+// mod m_1, X = v_0 + m_0 v_1 < M; the signed representative in (-M/2, M/2].
+template <int K>
+__device__ __forceinline__ long long garner32(const Exact32 &a, uint32_t r0, uint32_t r1)
+{
+    uint64_t X = r0;
+    if constexpr (K == 2) {
+        const uint32_t m1 = a.m[1];
+        uint32_t vq = shoup32(r0, 1u, a.onep[1], m1);
+        vq = vq >= m1 ? vq - m1 : vq;                               // v_0 mod m_1
+        const uint32_t d = r1 >= vq ? r1 - vq : r1 + m1 - vq;
+        uint32_t v1 = shoup32(d, a.inv01, a.inv01p, m1);
+        v1 = v1 >= m1 ? v1 - m1 : v1;
+        X += (uint64_t)v1 * a.m[0];
+    }
+    return X > a.half ? (long long)(X - a.M) : (long long)X;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_exact_garner32(const __grid_constant__ Exact32 a, long long *__restrict__ h)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long n4 = a.n / 4;
+    for (long long q = tid; q < n4; q += nthr) {
+        const uint4 u = __ldcs(reinterpret_cast<const uint4 *>(a.rf[0]) + q);
+        const uint4 w = K == 2 ? __ldcs(reinterpret_cast<const uint4 *>(a.rf[1]) + q) : make_uint4(0, 0, 0, 0);
+        longlong2 *o = reinterpret_cast<longlong2 *>(h) + 2 * q;
+        __stcs(o, make_longlong2(garner32<K>(a, u.x, w.x), garner32<K>(a, u.y, w.y)));
+        __stcs(o + 1, make_longlong2(garner32<K>(a, u.z, w.z), garner32<K>(a, u.w, w.w)));
+    }
+    for (long long i = 4 * n4 + tid; i < a.n; i += nthr)
+        h[i] = garner32<K>(a, a.rf[0][i], K == 2 ? a.rf[1][i] : 0u);
+}
+
 __global__ void k_exact_residues(const __grid_constant__ ExactArgs a, const long long *__restrict__ f,
                                  const long long *__restrict__ g, void *const *outf, void *const *outg)
 {
@@ -176,6 +277,8 @@ struct ntt_exact_s {
     void *host_ptrs[2 * KMAX] = {};   // the same pointers, host side
     int nsm = 0;
     bool fused = false;               // whole sequences, 32-bit primes: residues and Garner fused into the convolutions
+    bool all32 = false;               // every prime below 2^25: the 32-bit residue and reconstruction kernels
+    Exact32 a32{};
 };
 
 extern "C" void ntt_exact_destroy(ntt_exact_t e)
@@ -261,6 +364,30 @@ extern "C" ntt_status ntt_exact_plan(uint32_t N, uint32_t bound_bits, ntt_exact_
     if (cudaMemcpy(e->ptrs_f, host, sizeof host, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(ntt_fail(NTT_ERR_CUDA, "ntt_exact_plan: upload"));
     memcpy(e->host_ptrs, host, sizeof host);
+    e->all32 = true;
+    for (int i = 0; i < e->k; ++i) e->all32 = e->all32 && a.p[i].word == 32 && a.p[i].m < (1ull << 25);
+    if (e->all32) {
+        Exact32 &b = e->a32;
+        b.k = e->k;
+        for (int i = 0; i < e->k; ++i) {
+            const uint64_t m = a.p[i].m;
+            b.m[i] = (uint32_t)m;
+            b.c[i] = (uint32_t)((1ull << 32) % m);
+            b.cp[i] = (uint32_t)(((uint64_t)b.c[i] << 32) / m);
+            b.onep[i] = (uint32_t)((1ull << 32) / m);
+            b.r64[i] = (uint32_t)a.p[i].r64;
+            b.rf[i] = (uint32_t *)host[i];
+            b.rg[i] = (uint32_t *)host[KMAX + i];
+        }
+        if (e->k == 2) {
+            b.inv01 = (uint32_t)a.inv[0][1];
+            b.inv01p = (uint32_t)(((uint64_t)b.inv01 << 32) / b.m[1]);
+        }
+        if (e->k <= 2) {
+            b.M = (unsigned long long)M;
+            b.half = (unsigned long long)half;
+        }
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -327,14 +454,28 @@ extern "C" ntt_status conv_exact(ntt_exact_t e, const int64_t *f, const int64_t 
             continue;
         }
         a.vec = ((((uintptr_t)fw | (uintptr_t)gw | (uintptr_t)hw) & 15u) == 0) ? 1 : 0;
-        k_exact_residues<<<grid, threads, 0, st>>>(a, fw, gw, e->ptrs_f, e->ptrs_g);
+        Exact32 b = e->a32;
+        b.n = a.n;
+        const bool fast = e->all32 && a.vec;
+        if (fast) {
+            switch (e->k) {
+            case 1: k_exact_residues32<1><<<grid, threads, 0, st>>>(b, fw, gw); break;
+            case 2: k_exact_residues32<2><<<grid, threads, 0, st>>>(b, fw, gw); break;
+            case 3: k_exact_residues32<3><<<grid, threads, 0, st>>>(b, fw, gw); break;
+            default: k_exact_residues32<4><<<grid, threads, 0, st>>>(b, fw, gw); break;
+            }
+        } else {
+            k_exact_residues<<<grid, threads, 0, st>>>(a, fw, gw, e->ptrs_f, e->ptrs_g);
+        }
         cudaError_t err = ntt::launched();
         if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: residues: %s", cudaGetErrorString(err));
         for (int i = 0; i < e->k; ++i) {
             ntt_status s = conv_circular(e->plans[i], e->host_ptrs[i], e->host_ptrs[KMAX + i], e->host_ptrs[i], np, stream);
             if (s != NTT_OK) return s;
         }
-        k_exact_garner<<<grid, threads, 0, st>>>(a, e->ptrs_f, hw);
+        if (fast && e->k == 1) k_exact_garner32<1><<<grid, threads, 0, st>>>(b, hw);
+        else if (fast && e->k == 2) k_exact_garner32<2><<<grid, threads, 0, st>>>(b, hw);
+        else k_exact_garner<<<grid, threads, 0, st>>>(a, e->ptrs_f, hw);
         err = ntt::launched();
         if (err != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "conv_exact: reconstruction: %s", cudaGetErrorString(err));
     }

@@ -106,6 +106,23 @@ def test_conv_exact_many_pairs_in_waves(ntt, orc):
     plan.close()
 
 
+@pytest.mark.parametrize("N,bound,big,small,batch", [(2, 40, 35, 3, 3), (1, 62, 54, 7, 7), (4, 62, 54, 5, 5)])
+def test_conv_exact_wide_inputs(ntt, orc, N, bound, big, small, batch):
+    """Inputs whose upper 32 bits are far from 0 and -1 (|f| near 2^big,
+    |g| <= 2^small, signs mixed): the residue of each half of the bits, the
+    correction for negative inputs, the four-element path and the tail."""
+    plan = ntt.ExactPlan(N, bound)
+    rng = np.random.default_rng(big + N)
+    f = rng.integers(-(1 << big), 1 << big, size=(batch, N), dtype=np.int64)
+    g = rng.integers(-(1 << small), 1 << small, size=(batch, N), dtype=np.int64)
+    f[0, 0], g[0, 0] = -(1 << big), 1 << small           # the extremes
+    assert int(np.abs(f).max()) * int(np.abs(g).max()) * N < 1 << bound
+    h = ntt.conv_exact(plan, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    for b in range(batch):
+        assert np.array_equal(h[b], orc.int_conv(f[b], g[b])), b
+    plan.close()
+
+
 def test_conv_exact_rejects_uncoverable_bound(ntt):
     with pytest.raises(ntt.NttError):
         ntt.ExactPlan(1 << 20, 63)
