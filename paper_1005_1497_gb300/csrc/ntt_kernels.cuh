@@ -628,12 +628,24 @@ __global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(const __grid_constant__ N
     const W scale = INV ? a.c.ninv : (W)1;
     const W scalep = INV ? a.c.ninvp : a.c.onep;
 
-    for (long long rho = (long long)blockIdx.x * GPC + gid; rho < a.batch; rho += (long long)gridDim.x * GPC) {
-        const W *xp = a.x + (size_t)rho * N;
-        W *yp = a.y + (size_t)rho * N;
-        W v[1][R];
+    // 32-bit words: the next sequence is loaded into w while this one is
+    // transformed (every group of a block otherwise waits on its loads at
+    // the same time); 64-bit words have no registers to spare for it
+    constexpr bool PF = sizeof(W) == 4;
+    const long long step = (long long)gridDim.x * GPC;
+    long long rho = (long long)blockIdx.x * GPC + gid;
+    W v[1][R], w[R];
+    auto load = [&](long long r, W (&dst)[R]) {
+        const W *xp = a.x + (size_t)r * N;
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[0][k] = xp[b0 + ((uint32_t)k << lo0)];
+        for (int k = 0; k < R; ++k) dst[k] = xp[b0 + ((uint32_t)k << lo0)];
+    };
+    if (PF && rho < a.batch) load(rho, v[0]);
+    for (; rho < a.batch; rho += step) {
+        W *yp = a.y + (size_t)rho * N;
+        if (!PF) load(rho, v[0]);
+        const bool more = PF && rho + step < a.batch;
+        if (more) load(rho + step, w);
         fwd_all<W, L, L, 0, 1, TW_SMEM>(v, 0u, tau, S, gid, stw, a.c);
         group_sync<T>(gid);
 #pragma unroll
@@ -648,6 +660,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(const __grid_constant__ N
             const uint32_t u = b0 + ((uint32_t)k << lo0);
             W val = csub<W>(shoup<W>(S[G::pad(u)], scale, scalep, a.c.m), a.c.m);
             yp[INV ? ((N - u) & (N - 1u)) : u] = val;
+        }
+        if (more) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) v[0][k] = w[k];
         }
     }
 }
