@@ -279,6 +279,17 @@ cudaError_t Launch<W>::rows_fwd(int L, const RowArgs<W> &a, int grid, cudaStream
 }
 
 template <typename W>
+cudaError_t Launch<W>::rows_uni(const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+    constexpr int LR = LRMax<W>::v;
+    constexpr size_t smem = TwBytes<W, LR>::v + RowShape<W, LR, LR>::smem(1);
+    static const cudaError_t init = ensure_smem(k_rows_uni<W, LR>, smem);
+    if (init != cudaSuccess) return init;
+    k_rows_uni<W, LR><<<grid, BLOCK, smem, st>>>(a);
+    return launched();
+}
+
+template <typename W>
 cudaError_t Launch<W>::cols_fwd(int L, int ns, int src, bool twisted, const ColArgs<W> &a, cudaStream_t st)
 {
     if (ns == 2 && src == 0 && twisted) {
@@ -299,6 +310,10 @@ cudaError_t Launch<W>::cols_fwd(int L, int ns, int src, bool twisted, const ColA
 #undef C
     } else if (ns == 1 && src == 0 && !twisted) {
 #define C(X) launch_cols_fwd<W, X, 1, 0, false>(a, st)
+        NTT_SWITCH_L(C)
+#undef C
+    } else if (ns == 1 && src == 0) {
+#define C(X) launch_cols_fwd<W, X, 1, 0, true>(a, st)
         NTT_SWITCH_L(C)
 #undef C
     }

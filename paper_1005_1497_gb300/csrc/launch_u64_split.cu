@@ -5,4 +5,5 @@ template cudaError_t Launch<uint64_t>::conv_rows_split(int, bool, const RowArgs<
 template cudaError_t Launch<uint64_t>::cols_fwd(int, int, int, bool, const ColArgs<uint64_t> &, cudaStream_t);
 template cudaError_t Launch<uint64_t>::cols_inv(int, int, bool, const ColArgs<uint64_t> &, cudaStream_t);
 template cudaError_t Launch<uint64_t>::rows_fwd(int, const RowArgs<uint64_t> &, int, cudaStream_t);
+template cudaError_t Launch<uint64_t>::rows_uni(const RowArgs<uint64_t> &, int, cudaStream_t);
 }  // namespace ntt

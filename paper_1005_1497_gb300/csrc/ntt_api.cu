@@ -344,12 +344,17 @@ static cudaError_t ntt_dispatch(ntt_plan_t p, const W *x, W *y, long long batch,
     const long long wave = (long long)p->wave * 2;     // one sequence per pair: twice the pairs fit
     for (long long w0 = 0; w0 < batch; w0 += wave) {
         const long long np = std::min<long long>(wave, batch - w0);
-        ColArgs<W> ca{x, nullptr, nullptr, scratch, nullptr, nullptr, np, w0, tw, c};
-        cudaError_t e = Launch<W>::cols_fwd(p->L, 1, 0, false, ca, st);
+        // the plan's form: the twist (whole-row trees with the uniform table)
+        // or row-dependent twiddles; both leave the same tree order
+        const bool twisted = p->twist;
+        ColArgs<W> ca{x, nullptr, nullptr, scratch, nullptr, nullptr, np, w0, tw, c, (const W *)p->pw,
+                      (const W *)p->pwl, (const W *)p->pd};
+        cudaError_t e = Launch<W>::cols_fwd(p->L, 1, 0, twisted, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);
         RowArgs<W> ra{scratch, nullptr, nullptr, nullptr, rows, 0, tw, c};
-        e = Launch<W>::rows_fwd(p->L, ra, row_grid(p->nsm, rows, Launch<W>::rows_per_block(p->LR)), st);
+        const int grid = row_grid(p->nsm, rows, Launch<W>::rows_per_block(p->LR));
+        e = twisted ? Launch<W>::rows_uni(ra, grid, st) : Launch<W>::rows_fwd(p->L, ra, grid, st);
         if (e != cudaSuccess) return e;
         e = Launch<W>::bitrev_out(p->L, inv, scratch, y + (size_t)w0 * N, np, c, st);
         if (e != cudaSuccess) return e;

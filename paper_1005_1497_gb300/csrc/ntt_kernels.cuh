@@ -979,7 +979,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_rows_fwd(const __grid_constant__ R
     const int gid = threadIdx.x / T;
     const uint32_t tau = threadIdx.x % T;
     W *S = reinterpret_cast<W *>(smem_raw) + (size_t)gid * G::ROWP;
-    const uint32_t b0 = G::base(0, tau), bl = G::base(last, tau);
+    const uint32_t b0 = G::base(0, tau);
     for (long long rho = (long long)blockIdx.x * GPC + gid; rho < a.nrows; rho += (long long)gridDim.x * GPC) {
         const long long pw = rho >> (L - LR);
         const uint32_t row = (uint32_t)rho & ((1u << (L - LR)) - 1u);
@@ -988,8 +988,58 @@ __global__ void __launch_bounds__(BLOCK, 1) k_rows_fwd(const __grid_constant__ R
 #pragma unroll
         for (int k = 0; k < R; ++k) v[0][k] = p[b0 + ((uint32_t)k << G::lo(0))];
         fwd_all<W, L, LR, 0, 1, TW_GLOBAL>(v, row << LR, tau, S, gid, a.tw, a.c);
+        // back to the first pass's layout, where a warp's stores are contiguous
+        if constexpr (last > 0) exchange<W, LR, last, 0, 1>(v, S, tau, gid);
 #pragma unroll
-        for (int k = 0; k < R; ++k) p[bl + ((uint32_t)k << G::lo(last))] = v[0][k];
+        for (int k = 0; k < R; ++k) p[b0 + ((uint32_t)k << G::lo(0))] = v[0][k];
+    }
+}
+
+// Forward rows of the split path's twist form, for the natural-order
+// transforms: after the twisted column pass every row of 2^LR words is a
+// whole length-2^LR tree with the uniform table (the first 2^(LR-1) entries
+// of the plan's table), staged in shared memory.  In place, tree order: the
+// same layout as the row-dependent rows (X(brv(k) + 2^LC brv(j)) at row k,
+// position j), so the same bit-reversal gather follows.  32-bit words load
+// the next row while this one is transformed.
+template <typename W, int LR>
+__global__ void __launch_bounds__(BLOCK, 1) k_rows_uni(const __grid_constant__ RowArgs<W> a)
+{
+    using G = Geo<W, LR>;
+    constexpr int T = G::T, R = G::R, GPC = RowShape<W, LR, LR>::GPC;
+    constexpr int last = G::NPASS - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gid = threadIdx.x / T;
+    const uint32_t tau = threadIdx.x % T;
+    W *stw = reinterpret_cast<W *>(smem_raw);
+    W *S = reinterpret_cast<W *>(smem_raw + TwBytes<W, LR>::v) + (size_t)gid * G::ROWP;
+    const uint32_t b0 = G::base(0, tau);
+    stage_twiddles<W>(a.tw, stw, TwBytes<W, LR>::pairs);
+    __syncthreads();
+    constexpr bool PF = sizeof(W) == 4;
+    const long long step = (long long)gridDim.x * GPC;
+    long long rho = (long long)blockIdx.x * GPC + gid;
+    W v[1][R], w[R];
+    auto load = [&](long long r, W (&dst)[R]) {
+        const W *p = a.f + ((size_t)r << LR);
+#pragma unroll
+        for (int k = 0; k < R; ++k) dst[k] = p[b0 + ((uint32_t)k << G::lo(0))];
+    };
+    if (PF && rho < a.nrows) load(rho, v[0]);
+    for (; rho < a.nrows; rho += step) {
+        if (!PF) load(rho, v[0]);
+        const bool more = PF && rho + step < a.nrows;
+        if (more) load(rho + step, w);
+        fwd_all<W, LR, LR, 0, 1, TW_SMEM>(v, 0u, tau, S, gid, stw, a.c);
+        // back to the first pass's layout, where a warp's stores are contiguous
+        if constexpr (last > 0) exchange<W, LR, last, 0, 1>(v, S, tau, gid);
+        W *p = const_cast<W *>(a.f) + ((size_t)rho << LR);
+#pragma unroll
+        for (int k = 0; k < R; ++k) p[b0 + ((uint32_t)k << G::lo(0))] = v[0][k];
+        if (more) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) v[0][k] = w[k];
+        }
     }
 }
 

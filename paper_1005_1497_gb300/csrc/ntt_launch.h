@@ -24,6 +24,8 @@ template <typename W> struct Launch {
     static cudaError_t cols_fwd(int L, int ns, int src, bool twisted, const ColArgs<W> &a, cudaStream_t st);
     static cudaError_t cols_inv(int L, int dst, bool twisted, const ColArgs<W> &a, cudaStream_t st);
     static cudaError_t rows_fwd(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
+    // rows of the twist form for transforms: whole length-2^LRMAX trees in place
+    static cudaError_t rows_uni(const RowArgs<W> &a, int grid, cudaStream_t st);
     static cudaError_t bitrev_out(int L, bool inv, const W *src, W *dst, long long batch, const ModC<W> &c,
                                   cudaStream_t st);
     // natural-order transform of whole sequences (L <= LRMAX)

@@ -139,6 +139,23 @@ def test_ntt_forward_inverse(ntt, orc, m, L):
     assert np.array_equal(host(ntt.ntt_inverse(plan, dev(x, wb))), ref_ntt(orc, x, m, plan.omega, inverse=True))
 
 
+@pytest.mark.parametrize("m,L", [(M, 15), (M, 17), (M, 19), (M64, 14), (M64, 18), (M64, 20)])
+@pytest.mark.parametrize("form", ["0", "1"])
+def test_ntt_split_forms(ntt, orc, monkeypatch, m, L, form):
+    """Natural-order transforms above one block in both forms of the split
+    path (row-dependent twiddles; the four-step twist with whole-row trees),
+    one and two column passes, against the transform of Eq. 2 / Eq. 3."""
+    monkeypatch.setenv("NTT_SPLIT_TWIST", form)
+    N = 1 << L
+    plan = ntt.Plan(m, N)
+    assert plan.twist == (form == "1")
+    wb = plan.word_bits
+    x, _ = pairs(m, 2, N, seed=450 + L)
+    X = ntt.ntt_forward(plan, dev(x, wb))
+    assert np.array_equal(host(X), ref_ntt(orc, x, m, plan.omega))
+    assert np.array_equal(host(ntt.ntt_inverse(plan, X)), x)
+
+
 @pytest.mark.parametrize("m,L", [(M, 0), (M, 1), (M, 5), (M, 10), (M, 14), (M, 16), (M64, 11), (641, 6)])
 def test_conv_plain_form(ntt, orc, m, L):
     N = 1 << L
