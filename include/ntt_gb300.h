@@ -354,7 +354,7 @@ typedef struct {
  * log2 N + bits(max|f|) + bits(max|g|)).  The plan takes the cheapest primes
  * (32-bit words first) whose product M reaches 2^(bound_bits + 1), creates
  * one modular plan per prime and owns device scratch for a wave of pairs
- * (at most 256 MiB of residues).
+ * (at most 512 MiB of residues).
  * Errors: NTT_ERR_ARG (NULL out), NTT_ERR_LENGTH (N not a power of two, or
  * the primes that admit N cannot cover the bound), NTT_ERR_RANGE
  * (bound_bits outside 1..63), NTT_ERR_OOM, NTT_ERR_CUDA. */

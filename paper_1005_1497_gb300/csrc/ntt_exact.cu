@@ -345,10 +345,11 @@ extern "C" ntt_status ntt_exact_plan(uint32_t N, uint32_t bound_bits, ntt_exact_
     a.half_hi = (unsigned long long)(half >> 64);
     a.M_lo = (unsigned long long)M;
     a.M_hi = (unsigned long long)(M >> 64);
-    // scratch: waves of pairs, at most 256 MiB of residues
+    // scratch: waves of pairs, at most 512 MiB of residues (8192 pairs of
+    // 2^12 over two primes in one wave: fewer, fuller launches)
     size_t per_pair = 0;
     for (int i = 0; i < e->k; ++i) per_pair += 2 * (size_t)N * (a.p[i].word / 8);
-    e->wave = std::min<size_t>(65536, std::max<size_t>(1, ((size_t)256 << 20) / per_pair));
+    e->wave = std::min<size_t>(65536, std::max<size_t>(1, ((size_t)512 << 20) / per_pair));
     if (cudaMalloc(&e->scratch, e->wave * per_pair) != cudaSuccess ||
         cudaMalloc((void **)&e->ptrs_f, 2 * KMAX * sizeof(void *)) != cudaSuccess)
         return bail(ntt_fail(NTT_ERR_OOM, "ntt_exact_plan: scratch"));

@@ -94,14 +94,17 @@ def test_conv_exact_prime_choice(ntt):
 
 
 def test_conv_exact_many_pairs_in_waves(ntt, orc):
-    N, bound = 1 << 12, 40
+    """More pairs than one wave of the plan's scratch (a full wave and a
+    ragged second one)."""
+    N, bound = 1 << 16, 40
     plan = ntt.ExactPlan(N, bound)
-    batch = 3 * plan.wave // 2 if plan.wave < 4000 else 600
+    assert plan.wave < 2048
+    batch = plan.wave + 3
     amp = amp_for(N, bound)
     f, g = signed_inputs(batch, N, amp, seed=99)
     h = ntt.conv_exact(plan, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
-    for b in (0, 1, batch // 2, batch - 1):
-        idx = np.arange(0, N, 97, dtype=np.uint64)
+    for b in (0, 1, plan.wave - 1, plan.wave, batch - 1):
+        idx = np.arange(0, N, 4099, dtype=np.uint64)
         assert np.array_equal(h[b][idx.astype(np.int64)], orc.int_conv_sample(f[b], g[b], idx))
     plan.close()
 
