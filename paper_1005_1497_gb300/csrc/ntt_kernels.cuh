@@ -657,9 +657,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_ntt_rows(const __grid_constant__ N
         group_sync<T>(gid);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            const uint32_t u = b0 + ((uint32_t)k << lo0);
-            W val = csub<W>(shoup<W>(S[G::pad(u)], scale, scalep, a.c.m), a.c.m);
-            yp[INV ? ((N - u) & (N - 1u)) : u] = val;
+            // output index t (a warp's stores are one aligned run); the
+            // inverse takes its value from <-t>_N
+            const uint32_t t = b0 + ((uint32_t)k << lo0);
+            const uint32_t u = INV ? ((N - t) & (N - 1u)) : t;
+            yp[t] = csub<W>(shoup<W>(S[G::pad(u)], scale, scalep, a.c.m), a.c.m);
         }
         if (more) {
 #pragma unroll
