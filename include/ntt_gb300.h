@@ -115,7 +115,8 @@ typedef struct {
     uint32_t word_bits;  /* 32 or 64 */
     uint32_t four_step;  /* 1 when N exceeds one thread block and the split path is used */
     uint32_t wave;       /* pairs per scratch wave of the split path (0 if unused) */
-    uint32_t twist;      /* 1 when the split path of convolutions uses the four-step twist form */
+    uint32_t twist;      /* 1 when the split path (convolutions and natural-order transforms) uses
+                            the four-step twist form, 0 for row-dependent twiddles */
 } ntt_plan_info_t;
 
 /* Fill *info with the plan's parameters.  Errors: NTT_ERR_ARG. */

@@ -196,6 +196,25 @@ def test_in_place_and_deterministic(ntt, orc):
         assert np.array_equal(host(ft), h1)
 
 
+@pytest.mark.parametrize("m,L,batch", [(M, 10, 600), (M, 14, 400), (M, 17, 3), (M64, 12, 300), (M64, 18, 3)])
+def test_transforms_in_place(ntt, orc, m, L, batch):
+    """ntt_forward / ntt_inverse with the output aliasing the input, over
+    enough sequences that every row group loads a next one while its current
+    one is written; identical to the out-of-place results."""
+    N = 1 << L
+    plan = ntt.Plan(m, N)
+    wb = plan.word_bits
+    x, _ = pairs(m, batch, N, seed=650 + L)
+    xt = dev(x, wb)
+    X = ntt.ntt_forward(plan, xt)
+    y = xt.clone()
+    ntt.ntt_forward(plan, y, out=y)
+    assert torch.equal(y, X)
+    ntt.ntt_inverse(plan, y, out=y)
+    assert torch.equal(y, xt)
+    assert np.array_equal(host(X[:1]), ref_ntt(orc, x[:1], m, plan.omega))
+
+
 def test_conv_batched_uneven(ntt, orc):
     lens = inputs.log_uniform_lengths(60, 0, 19, seed=7)
     triples, ref = [], []
