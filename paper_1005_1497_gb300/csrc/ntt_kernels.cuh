@@ -842,30 +842,30 @@ __global__ void __launch_bounds__(256, (TWIST && NS == 2 && sizeof(W) == 4) ? 3 
             df[x] = csub<W>(shoup<W>(vf[k], z, zp, a.c.m), a.c.m);
             dg[x] = csub<W>(shoup<W>(vg[k], z, zp, a.c.m), a.c.m);
         }
-        return;
-    }
+    } else {
 #pragma unroll 1
-    for (int s = 0; s < NS; ++s) {
-        const W *src = source(s);
-        W *dst = (s == 0 ? a.dst0 : a.dst1) + (size_t)pw * N;
-        W v[RC];
+        for (int s = 0; s < NS; ++s) {
+            const W *src = source(s);
+            W *dst = (s == 0 ? a.dst0 : a.dst1) + (size_t)pw * N;
+            W v[RC];
 #pragma unroll
-        for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
-        col_fwd_levels<W, L, LR, L - LR - 1>(v, a.tw, a.c);
-        if constexpr (TWIST) {
+            for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
+            col_fwd_levels<W, L, LR, L - LR - 1>(v, a.tw, a.c);
+            if constexpr (TWIST) {
 #pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                W z, zp;
-                ld_pair_g<W>(a.pd + 2 * (size_t)(col + ((uint32_t)k << LR)), z, zp);
-                v[k] = csub<W>(shoup<W>(v[k], z, zp, a.c.m), a.c.m);
-                // 64-bit words: keep the compiler from hoisting every table
-                // load ahead of the products (it spills them otherwise)
-                if constexpr (sizeof(W) == 8 && RC > 8)
-                    if ((k & 7) == 7) asm volatile("" ::: "memory");
+                for (int k = 0; k < RC; ++k) {
+                    W z, zp;
+                    ld_pair_g<W>(a.pd + 2 * (size_t)(col + ((uint32_t)k << LR)), z, zp);
+                    v[k] = csub<W>(shoup<W>(v[k], z, zp, a.c.m), a.c.m);
+                    // 64-bit words: keep the compiler from hoisting every table
+                    // load ahead of the products (it spills them otherwise)
+                    if constexpr (sizeof(W) == 8 && RC > 8)
+                        if ((k & 7) == 7) asm volatile("" ::: "memory");
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < RC; ++k) dst[col + ((uint32_t)k << LR)] = v[k];
+            for (int k = 0; k < RC; ++k) dst[col + ((uint32_t)k << LR)] = v[k];
+        }
     }
 }
 
