@@ -690,17 +690,19 @@ template <typename W> struct ColArgs {
     const W *pd;        // one column pass: (w^(brv(k) t), quotient) at x = t + k 2^LR
 };
 
-// The four-step twist, one of the two forms of a convolution's split path
-// (the plan picks one per word size and length; the autotuner measures
-// both).  In the other form the rows read their node twiddles, which then
-// depend on the row, from the plan's table.  With the twist: after the column
-// levels, element (r, t) -- r the top L - LR index bits at their tree
-// position, t the low LR bits -- is multiplied by w^(brv(r) t).  That turns
-// every row's remaining levels into the length-2^LR transform with the
-// uniform table z'_i = w'^brv(i), w' = w^(2^(L-LR)), whose entries are the
-// first 2^(LR-1) of the plan's table; the rows then run the whole-sequence
-// kernel.  The inverse (the transposed tree) applies the same diagonal
-// between the rows and the transposed column levels.  Output in [0, 2m).
+// The four-step twist, one of the two forms of the split path of
+// convolutions and natural-order transforms (the plan picks one per word
+// size and length; the autotuner measures both).  In the other form the rows
+// read their node twiddles, which then depend on the row, from the plan's
+// table.  With the twist: after the column levels, element (r, t) -- r the
+// top L - LR index bits at their tree position, t the low LR bits -- is
+// multiplied by w^(brv(r) t).  That turns every row's remaining levels into
+// the length-2^LR transform with the uniform table z'_i = w'^brv(i),
+// w' = w^(2^(L-LR)), whose entries are the first 2^(LR-1) of the plan's
+// table; the rows then run the whole-sequence convolution kernel (or, for
+// transforms, k_rows_uni).  The inverse (the transposed tree) applies the
+// same diagonal between the rows and the transposed column levels.  Output
+// in [0, 2m).
 //
 // With one column pass the factor of element x = t + k 2^LR depends on x
 // alone (not on the pair), so the plan stores it at x (ColArgs::pd): one
