@@ -223,8 +223,15 @@ void or_conv(const uint64_t *f, const uint64_t *g, uint64_t *h, uint64_t N, uint
 void or_conv_sample(const uint64_t *f, const uint64_t *g, uint64_t N, uint64_t m,
                     const uint64_t *idx, uint64_t count, uint64_t *out)
 {
-    for (uint64_t i = 0; i < count; i++)
+    for (uint64_t i = 0; i < count; i++) {
+#if ORACLE_MUTANT == 8
+        out[i] = or_conv_at(f, g, N, m, i % N);                 /* list position, not the index */
+#elif ORACLE_MUTANT == 9
+        out[i] = or_conv_at(f, g, N, m, (idx[i] + 1) % N);      /* off by one output */
+#else
         out[i] = or_conv_at(f, g, N, m, idx[i] % N);
+#endif
+    }
 }
 
 /* The convolution theorem with the direct transforms: Eq. 2 on f and g, the

@@ -226,6 +226,40 @@ def pin_fast_matches_direct(o):
             assert np.array_equal(o.fast_ntt(f, m, w), o.ntt(f, m, w))
 
 
+def pin_conv_sample(o):
+    # The sampler evaluates Eq. 1 at a list of output indices (read modulo N,
+    # the circular index of reading R5).  Three independent anchors:
+    #  - an impulse at k: h(j) = g(<j - k>_N) in closed form;
+    #  - the full direct convolution, itself pinned above, at the same indices;
+    #  - the radix-2 convolution (a different algorithm) at a length where the
+    #    full direct one is slow.
+    # The index lists are repeated, out of order and past N, so a sampler
+    # that reads the list position, drops the reduction or shifts an index fails.
+    r = _rng(6)
+    for m, nmax in [(641, 64), (2424833, 1024), (M, 1 << 19), (M64, 1 << 20)]:
+        N = min(64, nmax)
+        g = r.integers(0, m, N, dtype=np.uint64)
+        idx = np.array([N - 1, 0, 5, 5, 2 * N + 3, N, 17 % N, 1], dtype=np.uint64)
+        for k in (0, 1, N - 1, 9 % N):
+            d = np.zeros(N, dtype=np.uint64)
+            d[k] = 1
+            got = o.conv_sample(d, g, m, idx)
+            assert [int(v) for v in got] == [int(g[(int(j) - k) % N]) for j in idx]
+        f = r.integers(0, m, N, dtype=np.uint64)
+        full = o.conv(f, g, m)
+        perm = np.concatenate([r.permutation(N), r.integers(0, 4 * N, 16)]).astype(np.uint64)
+        got = o.conv_sample(f, g, m, perm)
+        assert [int(v) for v in got] == [int(full[int(j) % N]) for j in perm]
+    m, nmax, N = M, 1 << 19, 1 << 12
+    w = o.root(m, N, nmax)
+    f = r.integers(0, m, N, dtype=np.uint64)
+    g = r.integers(0, m, N, dtype=np.uint64)
+    fast = o.fast_conv(f, g, m, w)
+    idx = r.integers(0, 3 * N, 64).astype(np.uint64)
+    assert [int(v) for v in o.conv_sample(f, g, m, idx)] == [int(fast[int(j) % N]) for j in idx]
+    assert o.conv_sample(f, g, m, np.zeros(0, dtype=np.uint64)).shape == (0,)
+
+
 def pin_prime64(o):
     assert M64 == 33629 * (1 << 21) + 1           # Euler form k * 2^(n+2) + 1, n = 19
     assert o.is_prime(M64)

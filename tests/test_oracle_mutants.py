@@ -7,6 +7,8 @@ mutation define) and check that the pin suite rejects every one of them:
     5  the last term of the sum in Eq. 1 dropped
     6  g(j+k) instead of g(j-k) in the exact integer convolution
     7  the modulus-free transform not truncated to alpha bits
+    8  the sampled Eq. 1 evaluated at the list position instead of the listed index
+    9  the sampled Eq. 1 evaluated one output index too far
 """
 import os
 
@@ -40,6 +42,15 @@ def test_exact_and_modulus_free_mutant_is_caught(tmp_path, mutant):
         except AssertionError:
             failed += 1
     assert failed, f"mutant {mutant} passed every pin"
+
+
+@pytest.mark.parametrize("mutant", [8, 9])
+def test_sampler_mutant_is_caught(tmp_path, mutant):
+    so = oracle.build(out=os.path.join(tmp_path, f"mut{mutant}.so"), defines={"ORACLE_MUTANT": mutant})
+    o = oracle.Oracle(oracle.load(so))
+    assert P.run_pins(o, [P.pin_conv_sample]), f"mutant {mutant} passed the sampler pin"
+    # the mutation touches the sampler only: the full convolution pins still pass
+    assert P.run_pins(o, [P.pin_hand_example, P.pin_conv_closed_forms]) == []
 
 
 def test_real_oracle_passes_fast_subset(orc):
