@@ -317,12 +317,18 @@ void ntt_server_destroy(ntt_server_t srv);
  * more than the array is rejected with NTT_ERR_ARG (no supported length
  * does today).  The plan must be created beforehand (ntt_plan allocates).
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the one array
- * and it keeps the last call's contents; nothing in it needs clearing, but
- * calls whose work overlaps on the GPU (other streams, other threads) race
- * on it and must be serialised by the caller.
+ * The first call on a device is a set-up step: it looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, and
+ * under CUDA's lazy module loading that lookup is what loads the array's
+ * module and reserves its 16 MiB, which may synchronise the device.  Make
+ * one call during initialisation (a batch of one pair is enough), and
+ * before any stream capture; later calls only reuse the cached address.
+ * The address, like every plan, does not survive cudaDeviceReset.  The
+ * plan's device must be the current device (NTT_ERR_ARG otherwise).
+ * All calls on a device share the one array and it keeps the last call's
+ * contents; nothing in it needs clearing, but calls whose work overlaps on
+ * the GPU (other streams, other threads) race on it and must be serialised
+ * by the caller.
  * Errors: NTT_ERR_ARG, NTT_ERR_CUDA. */
 ntt_status conv_circular_noalloc(ntt_plan_t plan, const void *f_dev, const void *g_dev, void *h_dev,
                                  size_t batch, ntt_stream_t stream);

@@ -191,9 +191,9 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
             memcpy(&host[2 * i * elt], a, sizeof a);
         }
     }
-    if (cudaMalloc(&p->tw, host.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twiddle table");
+    if (!ntt::dev_alloc(&p->tw, host.size())) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twiddle table");
     CUDA_TRY(cudaMemcpy(p->tw, host.data(), host.size(), cudaMemcpyHostToDevice), "ntt_plan: upload twiddles");
-    if (cudaMalloc(&p->counter, sizeof(unsigned long long)) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: counter");
+    if (!ntt::dev_alloc(&p->counter, sizeof(unsigned long long))) return ntt_fail(NTT_ERR_OOM, "ntt_plan: counter");
     if (word == 32) fill_modc(p->c32, m, p->n_inv);
     else fill_modc(p->c64, m, p->n_inv);
 
@@ -217,7 +217,7 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         if (const char *env = getenv("NTT_SPLIT_TWIST")) p->twist = atoi(env) != 0;   // explicit override
         if (wave < 1) wave = 1;
         p->wave = (uint32_t)wave;
-        if (cudaMalloc(&p->scratch, 2 * wave * N * elt) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: scratch");
+        if (!ntt::dev_alloc(&p->scratch, 2 * wave * N * elt)) return ntt_fail(NTT_ERR_OOM, "ntt_plan: scratch");
         // powers w^e, e < N, for the twist between the column and row passes
         // (w^e = 2^{e N_Max / N}, again from the doubling sequence)
         std::vector<uint64_t> all = nt::powers_of_two_by_doubling((nmax / N) * (uint64_t)N, m);
@@ -232,7 +232,7 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
                 memcpy(&tab[2 * e * elt], a, sizeof a);
             }
         }
-        if (cudaMalloc(&p->pw, tab.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: power table");
+        if (!ntt::dev_alloc(&p->pw, tab.size())) return ntt_fail(NTT_ERR_OOM, "ntt_plan: power table");
         CUDA_TRY(cudaMemcpy(p->pw, tab.data(), tab.size(), cudaMemcpyHostToDevice), "ntt_plan: upload powers");
         if (L - p->LR <= 5) {
             // one column pass: element x = t + k 2^LR (t < 2^LR, k < 2^(L-LR))
@@ -247,7 +247,7 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
                 const size_t e = (sk * t) % N;
                 memcpy(&dg[2 * x * elt], &tab[2 * e * elt], 2 * elt);
             }
-            if (cudaMalloc(&p->pd, dg.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twist diagonal");
+            if (!ntt::dev_alloc(&p->pd, dg.size())) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twist diagonal");
             CUDA_TRY(cudaMemcpy(p->pd, dg.data(), dg.size(), cudaMemcpyHostToDevice), "ntt_plan: upload twist diagonal");
         }
         const size_t ns = (size_t)1 << (L - p->LR);
@@ -265,7 +265,7 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
                     memcpy(&lt[2 * i * elt], a, sizeof a);
                 }
             }
-        if (cudaMalloc(&p->pwl, lt.size()) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "ntt_plan: lane power table");
+        if (!ntt::dev_alloc(&p->pwl, lt.size())) return ntt_fail(NTT_ERR_OOM, "ntt_plan: lane power table");
         CUDA_TRY(cudaMemcpy(p->pwl, lt.data(), lt.size(), cudaMemcpyHostToDevice), "ntt_plan: upload lane powers");
     }
     *out = p.release();
@@ -475,7 +475,7 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
     if (!p->stage || p->stage_pairs < chunk) {
         cudaFree(p->stage);
         p->stage = nullptr;
-        if (cudaMalloc(&p->stage, SLOTS * 3 * chunk * seq) != cudaSuccess) return ntt_fail(NTT_ERR_OOM, "conv_circular_host: staging");
+        if (!ntt::dev_alloc(&p->stage, SLOTS * 3 * chunk * seq)) return ntt_fail(NTT_ERR_OOM, "conv_circular_host: staging");
         p->stage_pairs = chunk;
         for (cudaStream_t &st : p->hstream)
             if (!st) CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
@@ -524,6 +524,8 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
 }
 
 int ntt_plan_log2(ntt_plan_t p) { return p ? p->L : -1; }
+
+int ntt_plan_device(ntt_plan_t p) { return p ? p->device : -1; }
 
 ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs, long long count, void *scratch, uint32_t wave,
                           cudaStream_t st)

@@ -133,7 +133,7 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
             ++pos;
         }
     }
-    if (cudaMalloc(&b->descs, host.size()) != cudaSuccess) return bail(ntt_fail(NTT_ERR_OOM, "ntt_batch_plan: descriptors"));
+    if (!ntt::dev_alloc(&b->descs, host.size())) return bail(ntt_fail(NTT_ERR_OOM, "ntt_batch_plan: descriptors"));
     if (cudaMemcpy(b->descs, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(ntt_fail(NTT_ERR_CUDA, "ntt_batch_plan: upload descriptors"));
 
@@ -143,7 +143,7 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
         ntt_plan_get_info(c.plan, &info);
         if (info.four_step) {
             c.wave = std::min<uint32_t>(info.wave, (uint32_t)c.count);
-            if (cudaMalloc(&c.scratch, 2 * (size_t)c.wave * ((size_t)1 << c.L) * elt) != cudaSuccess)
+            if (!ntt::dev_alloc(&c.scratch, 2 * (size_t)c.wave * ((size_t)1 << c.L) * elt))
                 return bail(ntt_fail(NTT_ERR_OOM, "ntt_batch_plan: scratch"));
         }
     }
@@ -170,8 +170,8 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
     }
     b->nitems = (int)items.size();
     if (b->nitems) {
-        if (cudaMalloc(&b->items, items.size() * sizeof(ntt::WorkItem)) != cudaSuccess ||
-            cudaMalloc(&b->counter, sizeof(int)) != cudaSuccess)
+        if (!ntt::dev_alloc(&b->items, items.size() * sizeof(ntt::WorkItem)) ||
+            !ntt::dev_alloc(&b->counter, sizeof(int)))
             return bail(ntt_fail(NTT_ERR_OOM, "ntt_batch_plan: work list"));
         if (cudaMemcpy(b->items, items.data(), items.size() * sizeof(ntt::WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(ntt_fail(NTT_ERR_CUDA, "ntt_batch_plan: upload work list"));

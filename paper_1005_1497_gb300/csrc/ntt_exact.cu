@@ -350,8 +350,8 @@ extern "C" ntt_status ntt_exact_plan(uint32_t N, uint32_t bound_bits, ntt_exact_
     size_t per_pair = 0;
     for (int i = 0; i < e->k; ++i) per_pair += 2 * (size_t)N * (a.p[i].word / 8);
     e->wave = std::min<size_t>(65536, std::max<size_t>(1, ((size_t)512 << 20) / per_pair));
-    if (cudaMalloc(&e->scratch, e->wave * per_pair) != cudaSuccess ||
-        cudaMalloc((void **)&e->ptrs_f, 2 * KMAX * sizeof(void *)) != cudaSuccess)
+    if (!ntt::dev_alloc(&e->scratch, e->wave * per_pair) ||
+        !ntt::dev_alloc((void **)&e->ptrs_f, 2 * KMAX * sizeof(void *)))
         return bail(ntt_fail(NTT_ERR_OOM, "ntt_exact_plan: scratch"));
     e->ptrs_g = e->ptrs_f + KMAX;
     void *host[2 * KMAX] = {};

@@ -4,10 +4,26 @@
 #include <cuda_runtime.h>
 #include "../../include/ntt_gb300.h"
 
+namespace ntt {
+// cudaMalloc that leaves no error behind when it fails: the library checks
+// every launch with cudaGetLastError(), which would otherwise report the
+// failed allocation again at the next (good) launch of this thread.
+template <typename T>
+inline bool dev_alloc(T **p, size_t bytes)
+{
+    if (cudaMalloc(reinterpret_cast<void **>(p), bytes) == cudaSuccess) return true;
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return false;
+}
+}  // namespace ntt
+
 // Record a message for ntt_last_error() and return s.
 ntt_status ntt_fail(ntt_status s, const char *fmt, ...);
 // log2 N of a plan.
 int ntt_plan_log2(ntt_plan_t p);
+// The device a plan was created on (its tables live there).
+int ntt_plan_device(ntt_plan_t p);
 // Library-owned plan for (m, N), created on first use.
 ntt_status ntt_cached_plan(uint64_t m, uint32_t N, ntt_plan_t *out);
 // Fused convolution of `count` pairs given by a device descriptor list

@@ -9,7 +9,10 @@
 // ntt_plan allocates; this entry point instead uses one fixed array that is
 // part of the library image on every GPU that loads it, so the call itself
 // allocates nothing.  (Creating the plan, which uploads the twiddle table,
-// is a set-up step that does allocate; do it during initialisation.)
+// is a set-up step that does allocate; do it during initialisation.  So is
+// the first call of this function on a device: it looks up the array's
+// device address, and under lazy module loading that lookup is what loads
+// this file's module and reserves the array, which can synchronise.)
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,12 +32,17 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};      // device address of g_noalloc_scratch, per device
 
 // Set-up, once per device with that device current: the host-side name of a
-// __device__ array is only a stand-in, so look up its device address.
-ntt_status scratch_address(void **out)
+// __device__ array is only a stand-in, so look up its device address.  The
+// plan's tables live on the plan's device, so that device must be the
+// current one (otherwise the kernels would reach across devices).
+ntt_status scratch_address(int plan_dev, void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return ntt_fail(NTT_ERR_CUDA, "conv_circular_noalloc: no usable current device");
+    if (dev != plan_dev)
+        return ntt_fail(NTT_ERR_ARG, "conv_circular_noalloc: the plan belongs to device %d but device %d is current",
+                        plan_dev, dev);
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
         void *p = nullptr;
@@ -65,7 +73,7 @@ extern "C" ntt_status conv_circular_noalloc(ntt_plan_t plan, const void *f_dev, 
         if (per_pair > kScratchBytes)
             return ntt_fail(NTT_ERR_ARG, "conv_circular_noalloc: N=%u needs %zu bytes of scratch per pair, "
                             "above the %zu-byte static scratch", info.N, per_pair, kScratchBytes);
-        s = scratch_address(&scratch);
+        s = scratch_address(ntt_plan_device(plan), &scratch);
         if (s != NTT_OK) return s;
         size_t w = kScratchBytes / per_pair;
         if (w > batch) w = batch;

@@ -310,17 +310,19 @@ extern "C" ntt_status ntt_server_create(uint64_t m, const ntt_server_config *cfg
         }
     }
     s->split_words = split_words;
-    if (cudaMalloc(&s->pool_mem, cfg->pool_bytes) != cudaSuccess) return bail(ntt_fail(NTT_ERR_OOM, "server: pool"));
+    if (!ntt::dev_alloc(&s->pool_mem, cfg->pool_bytes)) return bail(ntt_fail(NTT_ERR_OOM, "server: pool"));
     s->pool.init(cfg->pool_bytes);
     s->slots.resize(cfg->streams);
     for (Slot &slot : s->slots) {
         if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&slot.descs_dev, (size_t)cfg->max_batch * 3 * sizeof(void *)) != cudaSuccess ||
-            cudaHostAlloc(&slot.descs_host, (size_t)cfg->max_batch * 3 * sizeof(void *), cudaHostAllocDefault) != cudaSuccess)
+            !ntt::dev_alloc(&slot.descs_dev, (size_t)cfg->max_batch * 3 * sizeof(void *)) ||
+            cudaHostAlloc(&slot.descs_host, (size_t)cfg->max_batch * 3 * sizeof(void *), cudaHostAllocDefault) != cudaSuccess) {
+            (void)cudaGetLastError();          // (see ntt::dev_alloc)
             return bail(ntt_fail(NTT_ERR_OOM, "server: slot resources"));
+        }
         if (split_words) {
-            if (cudaMalloc(&slot.scratch, split_words * (s->word / 8)) != cudaSuccess)
+            if (!ntt::dev_alloc(&slot.scratch, split_words * (s->word / 8)))
                 return bail(ntt_fail(NTT_ERR_OOM, "server: split scratch"));
         }
     }

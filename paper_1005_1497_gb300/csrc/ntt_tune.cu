@@ -79,8 +79,8 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
         if (st) cudaStreamDestroy(st);
         ntt_plan_destroy(p);
     };
-    if (cudaMalloc(&f, batch * seq) != cudaSuccess || cudaMalloc(&g, batch * seq) != cudaSuccess ||
-        cudaMalloc(&h, batch * seq) != cudaSuccess) {
+    if (!ntt::dev_alloc(&f, batch * seq) || !ntt::dev_alloc(&g, batch * seq) ||
+        !ntt::dev_alloc(&h, batch * seq)) {
         cleanup();
         return ntt_fail(NTT_ERR_OOM, "ntt_autotune: buffers");
     }
@@ -100,7 +100,7 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
     int best_tw = (int)info.twist;
     for (uint32_t w : cand) {
         void *scratch = nullptr;
-        if (cudaMalloc(&scratch, 2 * (size_t)w * seq) != cudaSuccess) continue;   // too big: skip candidate
+        if (!ntt::dev_alloc(&scratch, 2 * (size_t)w * seq)) continue;   // too big: skip candidate
         for (int tw = 0; tw < 2; ++tw) {
             ntt_status r = ntt_conv_with_scratch(p, f, g, h, (long long)batch, scratch, w, st, tw);
             float ms = 0;

@@ -20,6 +20,8 @@ _lib = None
 NTT_OK = 0
 STATUS = {0: "NTT_OK", 1: "NTT_ERR_LENGTH", 2: "NTT_ERR_MODULUS", 3: "NTT_ERR_WORD", 4: "NTT_ERR_RANGE",
           5: "NTT_ERR_OOM", 6: "NTT_ERR_CUDA", 7: "NTT_ERR_TIMEOUT", 8: "NTT_ERR_ARG", 9: "NTT_ERR_ADMISSION"}
+STATUS_CODES = {name: code for code, name in STATUS.items()}
+NTT_ERR_ARG = STATUS_CODES["NTT_ERR_ARG"]
 
 # Every function the header declares, with its ctypes signature.
 _VP, _U64, _U32, _SZ, _INT = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_int
