@@ -5,7 +5,10 @@ One step = one fused batched convolution (forward transforms of f and g,
 pointwise product with N^-1, inverse transform) over the whole workload,
 inputs resident in HBM.  Default workload: 4096 pairs, N = 2^14,
 m = 13631489, 32-bit words (the uniform-batch configuration).  Prints ONE
-JSON line on rank 0.
+JSON line on rank 0.  The default run also measures the other four
+workloads (one small convolution, the large transforms, the uneven batch and
+the serving mix) and attaches each under "configs"; --workload runs one of
+them alone as the line's own workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload conv2|conv1|conv3|conv4|serve5|exact6|shift7] [--quick]
@@ -13,6 +16,10 @@ JSON line on rank 0.
 Multi-GPU (torchrun): every rank convolves its own batch (independent pairs,
 no collective on the data path); the timing is the max over ranks and the
 value counts the pairs of all ranks (weak scaling).
+
+CPU baseline: the test oracle on the host cores -- its radix-2 convolution
+(O(N log N)) on whole pairs of the workload, threaded over pairs and on one
+thread, and its direct Eq. 1 (O(N^2)) on sampled outputs.
 """
 from __future__ import annotations
 
@@ -29,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 M = 13631489
+M64 = 70525124609
 METRIC = "circular convolutions/sec and NTT GB/s vs HBM peak, batched vs plain form, bit-exact"
 WORKLOADS = {
     # name: (batch, log2N, description)
@@ -44,25 +52,31 @@ WORKLOADS = {
     "exact6": (8192, 12, "exact integer filtering: 8192 pairs x N=2^12 of signed 16-bit samples and taps "
                          "(|h| <= 2^42), int64 in and out, Chinese remainder theorem over Rader primes"),
 }
+SUB_CONFIGS = ("conv1", "conv3", "conv4", "serve5")
 IMAD_PER_SM_CLK = 64          # 32-bit IMAD lanes per SM per clock (GB300: 18.98 T IMAD/s measured over 152 SMs)
 SLOTS_PER_MODMUL = 4          # Shoup product: IMAD.HI (2 issue slots of the IMAD pipe) + 2 IMAD
+SCHEDULE = os.path.join(ROOT, "paper_1005_1497_gb300", "schedules", "gb300.json")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="conv2", choices=sorted(WORKLOADS))
-    ap.add_argument("--quick", action="store_true", help="fused timing only (no plain form, e2e, CPU baseline)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--quick", action="store_true",
+                    help="fused timing only (no plain form, e2e, CPU baseline or other workloads)")
+    ap.add_argument("--no-configs", action="store_true", help="do not measure the other workloads")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle samples")
     ap.add_argument("--log2n", type=int, default=None,
                     help="override log2 N of the uniform workloads (conv1/conv2/conv3 shapes), e.g. for profiling")
     ap.add_argument("--batch", type=int, default=None, help="override the number of pairs of the uniform workloads")
     ap.add_argument("--schedule", default=None,
-                    help="split-path schedule file: loaded if it exists (no autotuning), else written after tuning")
-    return ap.parse_args()
+                    help="split-path schedule file: loaded if it exists (no autotuning), else written after tuning; "
+                         "default: the packaged GB300 schedule when present, else the plan's heuristic")
+    ap.add_argument("--tune", action="store_true", help="autotune the split-path classes before timing")
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ helpers
@@ -196,35 +210,117 @@ def traffic_from_profile(kernel_tag: str):
         return None
 
 
+def uniform_shape(name: str, args):
+    """(batch, log2 N, description) of a uniform workload, with the overrides."""
+    batch, L, desc = WORKLOADS[name]
+    if name in ("conv1", "conv2", "conv3") and (args.log2n is not None or args.batch is not None):
+        L = args.log2n if args.log2n is not None else L
+        batch = args.batch if args.batch is not None else batch
+        desc = f"uniform batch: {batch} pairs x N=2^{L}, m=13631489, uint32 (override)"
+    return batch, L, desc
+
+
+def config_of(name: str, args, world: int = 1) -> dict:
+    """The workload's `config` object; both arms print the same one."""
+    par = f"replicas x{world} (independent pairs per GPU)"
+    if name in ("conv1", "conv2", "conv3"):
+        batch, L, desc = uniform_shape(name, args)
+        big = 8 * batch * (1 << L) > (129 << 20)
+        return {"workload": desc, "batch_per_gpu": batch, "N": 1 << L, "m": M,
+                "l2": "inputs larger than L2; no flush" if big else
+                      "inputs smaller than L2: every step rereads them from L2 (no flush)",
+                "parallelism": par}
+    if name == "conv4":
+        return {"workload": WORKLOADS[name][2], "pairs": WORKLOADS[name][0], "m": M,
+                "l2": "inputs larger than L2 (6 GB of f+g); no flush", "parallelism": par}
+    if name == "serve5":
+        return {"workload": WORKLOADS[name][2], "offered_req_per_s": 20000.0, "m": M64, "parallelism": par}
+    batch, L, desc = WORKLOADS[name]
+    if name == "exact6":
+        return {"workload": desc, "batch_per_gpu": batch, "N": 1 << L,
+                "l2": "inputs larger than L2 (512 MiB of int64 f+g); no flush", "parallelism": par}
+    return {"workload": desc, "batch_per_gpu": batch, "N": 1 << L, "m": 641,
+            "l2": "inputs larger than L2 (1 GiB of f+g); no flush", "parallelism": par}
+
+
+def load_schedule(args, ntt) -> dict:
+    """Split-path schedules: the file given (or the packaged GB300 one) when it
+    exists; none (the plan's heuristic) otherwise."""
+    path = args.schedule if args.schedule else SCHEDULE
+    if path and os.path.exists(path):
+        ntt.ntt_autotune_load(path)
+        return {"loaded": os.path.relpath(path, ROOT)}
+    return {"loaded": None}
+
+
+def alu_peak_gmodmul(local: int, sm_max_mhz: float) -> float:
+    import torch
+    return torch.cuda.get_device_properties(local).multi_processor_count * IMAD_PER_SM_CLK * sm_max_mhz * 1e6 \
+        / SLOTS_PER_MODMUL / 1e9
+
+
 # --------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(f, g, m: int, budget_s: float, threads: int | None = None):
-    """Oracle (direct Eq. 1) throughput on the host cores, on a bounded sample
-    of the workload's pairs: consecutive blocks of output indices of
-    consecutive pairs, as many as fit the time budget.  Returns
-    (conv/s, threads, outputs computed, seconds)."""
+def oracle_rate_mixed(pairs, budget_s: float, kind: str = "direct", threads: int | None = None):
+    """Time the oracle on a list of pairs (f, g, m, kind_of_pair) on the host
+    cores and return (conv/s, threads, work done, wall s).
+
+    kind "direct": Eq. 1 on sampled outputs -- the modular or_conv_sample
+    ("mod" pairs) or the exact integer or_int_conv_sample ("int" pairs).
+    Every thread takes blocks of output indices round-robin over the pairs
+    (8 on the first visit of a pair, 256 after); a pair's time is its sampled
+    seconds scaled by N / outputs (each output costs N products).  Work done
+    counts outputs.
+
+    kind "fast": the oracle's radix-2 convolution (or_fast_conv) on whole
+    pairs, round-robin, each pair at least once; a pair's time is the mean of
+    its runs.  Work done counts whole pairs.  ("int" pairs have no fast form
+    and are timed direct.)
+
+    Either way the rate is threads x pairs over the sum of the pairs' times,
+    which weighs every length of a mixed workload by its share of it."""
     import numpy as np
 
     import oracle
     o = oracle.Oracle()
     threads = threads or os.cpu_count() or 1
-    N = f.shape[1]
-    block = max(1, min(N, 256))
+    P = len(pairs)
     stop = time.perf_counter() + budget_s
     lock = threading.Lock()
-    state = {"next": 0, "done": 0}
+    nxt = [0]
+    cursor, spent, units = [0] * P, [0.0] * P, [0] * P
+    roots = {}
 
     def worker():
-        while time.perf_counter() < stop:
+        while True:
             with lock:
-                k = state["next"]
-                state["next"] += 1
-            pair, off = divmod(k * block, N)
-            pair %= f.shape[0]
-            idx = np.arange(off, off + block, dtype=np.uint64)
-            o.conv_sample(f[pair], g[pair], m, idx)
+                k = nxt[0]
+                if k >= P and time.perf_counter() >= stop:
+                    return
+                nxt[0] += 1
+                i = k % P
+                f, g, m, pk = pairs[i]
+                N = f.shape[-1]
+                fast = kind == "fast" and pk == "mod"
+                cnt = N if fast else min(N, 8 if k < P else 256)
+                off = cursor[i]
+                cursor[i] = (off + cnt) % N
+                if fast and (m, N) not in roots:
+                    roots[(m, N)] = o.root(m, N)
+                w = roots.get((m, N))
+            t = time.perf_counter()
+            if fast:
+                o.fast_conv(f, g, m, w)
+            else:
+                idx = ((off + np.arange(cnt, dtype=np.uint64)) % np.uint64(N)).astype(np.uint64)
+                if pk == "int":
+                    o.int_conv_sample(f, g, idx)
+                else:
+                    o.conv_sample(f, g, m, idx)
+            dt = time.perf_counter() - t
             with lock:
-                state["done"] += block
+                spent[i] += dt
+                units[i] += cnt
 
     t0 = time.perf_counter()
     ths = [threading.Thread(target=worker) for _ in range(threads)]
@@ -233,7 +329,64 @@ def cpu_oracle_rate(f, g, m: int, budget_s: float, threads: int | None = None):
     for t in ths:
         t.join()
     el = time.perf_counter() - t0
-    return state["done"] / N / el, threads, state["done"], el
+    est = sum(spent[i] * pairs[i][0].shape[-1] / units[i] for i in range(P))
+    done = sum(units) if kind != "fast" else sum(u // pairs[i][0].shape[-1] for i, u in enumerate(units))
+    return threads * P / est, threads, done, el
+
+
+def reference_pairs(name: str, args, cap: int = 64):
+    """Up to `cap` pairs of the workload, from the same seeded generators, in
+    the workload's own length mix.  Returns (pairs, unit)."""
+    import numpy as np
+
+    from paper_1005_1497_gb300 import inputs
+    if name == "conv4":
+        lens = inputs.log_uniform_lengths(WORKLOADS["conv4"][0], 6, 19, seed=1000)[:cap]
+        return [(*(a[0] for a in inputs.pairs(M, 1, int(n), seed=1000 + i)), M, "mod")
+                for i, n in enumerate(lens)], "conv/s"
+    if name == "serve5":
+        lens = inputs.log_uniform_lengths(512, 8, 18, seed=2000)[:cap]
+        return [(*(a[0] for a in inputs.pairs(M64, 1, int(n), seed=2000 + i, dtype=np.uint64)), M64, "mod")
+                for i, n in enumerate(lens)], "req/s"
+    if name == "exact6":
+        batch, L, _ = WORKLOADS[name]
+        N, amp = 1 << L, 1 << 15
+        out = []
+        for i in range(min(batch, cap)):
+            f = inputs.uniform_mod(2 * amp + 1, N, 1000 + i, 0, dtype=np.uint64).astype(np.int64) - amp
+            g = inputs.uniform_mod(2 * amp + 1, N, 1000 + i, 1, dtype=np.uint64).astype(np.int64) - amp
+            out.append((f, g, 0, "int"))
+        return out, "conv/s"
+    if name == "shift7":
+        batch, L, _ = WORKLOADS[name]
+        f, g = inputs.pairs(641, min(batch, cap), 1 << L, seed=1000)
+        return [(f[i], g[i], 641, "mod") for i in range(f.shape[0])], "conv/s"
+    batch, L, _ = uniform_shape(name, args)
+    f, g = inputs.pairs(M, min(batch, cap), 1 << L, seed=1000)
+    return [(f[i], g[i], M, "mod") for i in range(f.shape[0])], "conv/s"
+
+
+def cpu_baseline(name: str, args, budget_s: float, full: bool) -> dict:
+    """The oracle's rates on the workload's own pairs (rank 0 at N=1 only):
+    the radix-2 convolution threaded over pairs (the value), and with `full`
+    the same on one thread and the direct Eq. 1 on sampled outputs."""
+    pairs, unit = reference_pairs(name, args)
+    integer = pairs[0][3] == "int"
+    share = budget_s / (3 if full else 1)
+    rate, thr, done, el = oracle_rate_mixed(pairs, share, kind="fast")
+    what = ("exact integer Eq. 1 in 128-bit integers (oracle or_int_conv_sample), sampled outputs" if integer else
+            "radix-2 Cooley-Tukey convolution of the oracle (or_fast_conv) on whole pairs, threads over pairs")
+    out = {"value": round(rate, 4), "unit": unit, "cores": thr, "kind": "oracle",
+           "sample": f"{what}: {done} {'outputs' if integer else 'pair convolutions'} over {len(pairs)} pairs of the "
+                     f"workload in {el:.1f} s; rate = threads x pairs / sum of each pair's time"}
+    if full and not integer:
+        r1, _, d1, e1 = oracle_rate_mixed(pairs, share, kind="fast", threads=1)
+        out["single_thread"] = {"value": round(r1, 4), "cores": 1, "pairs_done": d1, "seconds": round(e1, 1)}
+        rd, thd, dd, ed = oracle_rate_mixed(pairs, share, kind="direct")
+        out["direct"] = {"value": round(rd, 4), "cores": thd,
+                         "sample": f"direct Eq. 1 (oracle or_conv_sample, O(N^2)) on {dd} sampled output indices "
+                                   f"of {len(pairs)} pairs in {ed:.1f} s, each pair's time scaled to all N outputs"}
+    return out
 
 
 # ---------------------------------------------------------------- our path
@@ -248,36 +401,28 @@ def count_launches(ntt, fn) -> int:
     return ntt.launch_count() - c0
 
 
-def run_ours(args):
+def measure_uniform(name, args, world, rank, local, sub=False):
+    """Uniform batches (conv1, conv2, conv3): one conv_circular per step."""
     import numpy as np
     import torch
 
     from paper_1005_1497_gb300 import inputs, ntt
 
-    world, rank, local = dist_setup()
-    if args.workload == "conv4":
-        return run_uneven(args, world, rank, local)
-    if args.workload == "serve5":
-        return run_serve(args, world, rank, local)
-    if args.workload == "exact6":
-        return run_exact(args, world, rank, local)
-    if args.workload == "shift7":
-        return run_shift(args, world, rank, local)
-    batch, L, desc = WORKLOADS[args.workload]
-    if args.log2n is not None or args.batch is not None:
-        L = args.log2n if args.log2n is not None else L
-        batch = args.batch if args.batch is not None else batch
-        desc = f"uniform batch: {batch} pairs x N=2^{L}, m=13631489, uint32 (override)"
+    batch, L, desc = uniform_shape(name, args)
     N = 1 << L
-    tuned = None
-    if L > 14:                                                    # split path: pick form and pairs per wave
-        if args.schedule and os.path.exists(args.schedule):
-            ntt.ntt_autotune_load(args.schedule)
-        else:
-            tuned = ntt.ntt_autotune(M, N, batch)
+    schedule = {}
+    if L > 14:                                                    # split path: form and pairs per wave
+        if args.tune and not sub:
+            t = ntt.ntt_autotune(M, N, batch)
+            schedule = {"tuned": {k: t[k] for k in ("wave", "twist", "default_wave", "default_twist")},
+                        "tuned_ms": round(t["ms"], 4), "heuristic_ms": round(t["default_ms"], 4)}
             if args.schedule:
                 ntt.ntt_autotune_save(args.schedule)
+        else:
+            schedule = load_schedule(args, ntt)
     plan = ntt.Plan(M, N)
+    if plan.four_step:
+        schedule.update({"pairs_per_wave": plan.wave, "twist_form": plan.twist})
     # inputs from the shared seeded generator (computed on the device), resident in HBM
     seed = 1000 + rank
     f = inputs.uniform_mod_torch(M, batch * N, seed, 0, device="cuda").view(batch, N)
@@ -306,7 +451,8 @@ def run_ours(args):
                 ntt.conv_circular(plan, f, g, out=h, stream=cap)
         torch.cuda.synchronize()
     run = graph.replay if graph is not None else step
-    for _ in range(max(args.warmup, 0)):
+    steps = args.steps if not sub else max(1, min(args.steps, 400 if L > 14 else 2000))
+    for _ in range(max(args.warmup, 3 if sub else 0)):
         run()
     torch.cuda.synchronize()
     barrier(world)
@@ -314,70 +460,75 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             run()
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     plain_launch_ms = None
     if graph is not None:
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         p1.record(stream)
         torch.cuda.synchronize()
-        plain_launch_ms = p0.elapsed_time(p1) / args.steps
+        plain_launch_ms = p0.elapsed_time(p1) / steps
     ms = max_over_ranks(world, ms)
     clocks = clk.summary()
     pairs_total = batch * world
     value = pairs_total * 1000.0 / ms
 
-    # roofline of the fused kernel (one launch per step when N fits one block)
+    # roofline: the fused kernel (one launch per step when N fits one block),
+    # or the split path's three kernels per wave, rows dominating
     hbm_peak, sm_max_mhz, peak_src = peaks()
     alg_bytes = 12.0 * N * batch                                 # f, g in, h out (uint32)
     modmul = batch * (3 * (N // 2) * L + N)                      # butterfly products + pointwise
     launch_ms = ms / launches_per_step
-    alu_peak = torch.cuda.get_device_properties(local).multi_processor_count * IMAD_PER_SM_CLK \
-        * sm_max_mhz * 1e6 / SLOTS_PER_MODMUL / 1e9               # G modmul/s
+    alu_peak = alu_peak_gmodmul(local, sm_max_mhz)
     alu_ach = modmul / (ms * 1e-3) / 1e9
     hbm_ach = alg_bytes / (ms * 1e-3) / 1e9
-    kernel_tag = f"k_conv_cr_u32_L{L}_{batch}x{N}"
-    traffic = traffic_from_profile(kernel_tag) if not plan.four_step else None
+    if plan.four_step:
+        kernel_tag = None
+        kernel = ("split path, per wave k_cols_fwd + k_conv_cr<u32,14,14,0,1> (rows: 2^(L-14) whole length-2^14 "
+                  "convolutions per pair, the dominant kernel) + k_cols_inv")
+    elif L > 10:
+        kernel_tag = f"k_conv_cr_u32_L{L}_{batch}x{N}"
+        kernel = f"k_conv_cr<u32,{L},{L},0,0> (fused, column/row form)"
+    else:
+        kernel_tag = None
+        kernel = f"k_conv_fused<u32,{L},0> (fused, one warp per sequence)"
+    traffic = traffic_from_profile(kernel_tag) if kernel_tag else None
     out = {
-        "metric": METRIC, "value": round(value, 1), "unit": "conv/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": round(value, 1), "unit": "conv/s", "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded counter-based uniform residues in [0,m))",
-        "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "m": M, "form": "fused batched",
-                   "l2": "inputs larger than L2 (512 MiB f+g at conv2); no flush",
-                   "parallelism": f"replicas x{world} (independent pairs per GPU)"},
+        "config": config_of(name, args, world),
         "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
                      "frac": round(alu_ach / alu_peak, 4), "traffic": traffic,
-                     "peak_src": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x SMs x {sm_max_mhz:.0f} MHz / {SLOTS_PER_MODMUL} slots per Shoup product",
-                     "kernel": kernel_tag if not plan.four_step else "split path (3 kernels per wave)",
-                     "launch_ms": round(launch_ms, 4)},
+                     "peak_src": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x SMs x {sm_max_mhz:.0f} MHz / {SLOTS_PER_MODMUL} "
+                                 f"slots per Shoup product",
+                     "kernel": kernel, "launch_ms": round(launch_ms, 4), "launches_per_step": launches_per_step},
         "roofline_hbm": {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(hbm_ach / hbm_peak, 4), "peak_src": f"{peak_src} copy bandwidth",
                          "algorithmic_bytes_per_step": alg_bytes},
         "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step * steps,
     }
+    if schedule:
+        out["schedule"] = schedule
     if graph is not None:
-        out["config"]["launch"] = "CUDA graph replay of one conv_circular call per step"
-        out["config"]["ms_per_step_plain_launch"] = round(plain_launch_ms, 4)
-    if tuned:
-        out["config"]["schedule"] = {"pairs_per_wave": tuned["wave"], "heuristic": tuned["default_wave"],
-                                     "twist": bool(tuned["twist"]), "heuristic_twist": bool(tuned["default_twist"]),
-                                     "tuned_ms": round(tuned["ms"], 4), "heuristic_ms": round(tuned["default_ms"], 4)}
+        out["launch"] = {"timed": "CUDA graph replay of one conv_circular call per step",
+                         "ms_per_step_plain_launch": round(plain_launch_ms, 4)}
 
-    if not args.quick:
+    if not args.quick and not sub:
         # standalone natural-order transforms of the same batch (Eq. 2 and 3):
         # 8 algorithmic bytes per element (read x, write X)
         X = torch.empty_like(f)
         tsteps = max(1, min(args.steps // 4, 200))
         ntt_rates = {}
-        for name, fn in (("forward", ntt.ntt_forward), ("inverse", ntt.ntt_inverse)):
+        for tname, fn in (("forward", ntt.ntt_forward), ("inverse", ntt.ntt_inverse)):
             for _ in range(3):
                 fn(plan, f, out=X, stream=stream)
             torch.cuda.synchronize()
@@ -389,8 +540,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             tms = max_over_ranks(world, t0e.elapsed_time(t1e) / tsteps)
             gbps = 8.0 * N * batch / (tms * 1e-3) / 1e9
-            ntt_rates[name] = {"ms": round(tms, 4), "GBps": round(gbps, 1), "frac_hbm": round(gbps / hbm_peak, 4),
-                               "transforms_per_s": round(batch * world * 1000.0 / tms, 1)}
+            ntt_rates[tname] = {"ms": round(tms, 4), "GBps": round(gbps, 1), "frac_hbm": round(gbps / hbm_peak, 4),
+                                "transforms_per_s": round(batch * world * 1000.0 / tms, 1)}
         out["ntt"] = ntt_rates
         del X
 
@@ -415,6 +566,7 @@ def run_ours(args):
                              "fused_speedup": round(pms / ms, 2), "bit_identical_to_fused": same}
         del work, h2
 
+    if not args.quick:
         # end to end through the host-buffer entry point (pinned host memory)
         fh = f.cpu().pin_memory()
         gh = g.cpu().pin_memory()
@@ -463,25 +615,52 @@ def run_ours(args):
                                        "both_directions_ms": round(both_ms, 3),
                                        "frac": round(both_ms / ems, 4),
                                        "note": "frac = the step's copies alone (both directions at once) / e2e step time"}
-        if world == 1 and rank == 0:
-            nb = min(batch, 64)
-            f_np, g_np = fh[:nb].numpy().view(np.uint32), gh[:nb].numpy().view(np.uint32)
-            rate, thr, done, el = cpu_oracle_rate(f_np, g_np, M, args.cpu_seconds)
-            out["cpu_baseline"] = {"value": round(rate, 4), "unit": "conv/s", "cores": thr, "kind": "oracle",
-                                   "sample": f"direct Eq. 1 (oracle or_conv_sample) on {done} output indices "
-                                             f"(= {done / N:.2f} of the {batch} length-{N} pairs) in {el:.1f} s"}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        if sub and plan.four_step:
+            out["noalloc"] = noalloc_ratio(ntt, plan, f, g, h, stream, min(steps, 50))
+        attach_cpu_baseline(out, name, args, world, rank, full=not sub)
+    return out
 
 
-def run_shift(args, world, rank, local):
+def noalloc_ratio(ntt, plan, f, g, h, stream, steps) -> dict:
+    """conv_circular_noalloc (split-path scratch in the library's fixed 16 MiB
+    array, so small waves) against conv_circular on the same batch."""
+    import ctypes
+
+    import torch
+    lib = ntt.lib()
+    out = torch.empty_like(h)
+
+    def call():
+        st = lib.conv_circular_noalloc(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), f.shape[0], ctypes.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise RuntimeError(lib.ntt_last_error().decode())
+
+    call()
+    torch.cuda.synchronize()
+    same = bool(torch.equal(out, h))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    na = e0.elapsed_time(e1) / steps
+    e0.record(stream)
+    for _ in range(steps):
+        ntt.conv_circular(plan, f, g, out=h, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    wave = (16 << 20) // (2 * plan.N * (plan.word_bits // 8))
+    return {"ms_per_step": round(na, 4), "conv_circular_ms": round(ms, 4), "ratio": round(na / ms, 3),
+            "pairs_per_wave": wave, "bit_identical": same}
+
+
+def measure_shift(args, world, rank, local, sub=False):
     """The strict bit-shift form (twiddles 2^e, e < 32, applied modulo F_5 =
     2^32 + 1 by shift and lo - hi; m = 641 divides F_5) against the same
     kernel with Shoup products modulo m and against the main fused path."""
-    import numpy as np
     import torch
 
     from paper_1005_1497_gb300 import inputs, ntt
@@ -524,8 +703,7 @@ def run_shift(args, world, rank, local):
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u64 lanes modulo F_5 (u32 in and out)",
            "data": "synthetic (seeded counter-based uniform residues in [0,641))",
-           "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "m": m,
-                      "l2": "inputs larger than L2 (1 GiB of f+g); no flush"},
+           "config": config_of("shift7", args, world),
            "roofline": {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(hbm_ach / hbm_peak, 4), "traffic": None, "peak_src": f"{peak_src} copy bandwidth",
                         "kernel": "k_conv_shift<32, 6, strict>", "algorithmic_bytes_per_step": alg_bytes},
@@ -555,16 +733,14 @@ def run_shift(args, world, rank, local):
                   "entry": "conv_circular_shift (strict) between one host-to-device copy of f and of g (pinned) "
                            "and one device-to-host copy of h",
                   "bit_identical_to_device_path": bool(torch.equal(hh, ref.cpu()))}
-    attach_cpu_baseline(out, args, world, rank)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    attach_cpu_baseline(out, "shift7", args, world, rank, full=False)
+    return out
 
 
-def run_exact(args, world, rank, local):
+def measure_exact(args, world, rank, local, sub=False):
     """Exact (non-modular) convolution of signed 16-bit data: residues modulo
     each prime of the plan, one fused modular convolution per prime, Garner
     reconstruction to int64."""
-    import numpy as np
     import torch
 
     from paper_1005_1497_gb300 import inputs, ntt
@@ -601,16 +777,14 @@ def run_exact(args, world, rank, local):
     hbm_peak, sm_max_mhz, peak_src = peaks()
     alg_bytes = 24.0 * N * batch                                   # int64 f, g in, h out
     modmul = batch * len(plan.primes) * (3 * (N // 2) * L + N)    # per prime: butterflies + pointwise
-    alu_peak = torch.cuda.get_device_properties(local).multi_processor_count * IMAD_PER_SM_CLK * sm_max_mhz * 1e6 \
-        / SLOTS_PER_MODMUL / 1e9
+    alu_peak = alu_peak_gmodmul(local, sm_max_mhz)
     alu_ach = modmul / (ms * 1e-3) / 1e9
     out = {"metric": METRIC, "value": round(batch * world * 1000.0 / ms, 1), "unit": "conv/s", "n_gpus": world,
            "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int64 (residues u32)",
            "data": "synthetic (seeded counter-based, uniform in [-2^15, 2^15])",
-           "config": {"workload": desc, "batch_per_gpu": batch, "N": N, "bound_bits": bound,
-                      "primes": plan.primes, "word_bits": plan.word_bits, "pairs_per_wave": plan.wave,
-                      "l2": "inputs larger than L2 (512 MiB of int64 f+g); no flush"},
+           "config": config_of("exact6", args, world),
+           "plan": {"bound_bits": bound, "primes": plan.primes, "word_bits": plan.word_bits, "pairs_per_wave": plan.wave},
            "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1),
                         "unit": "Gmodmul/s", "frac": round(alu_ach / alu_peak, 4), "traffic": None,
                         "kernel": "whole exact step (residues, one fused convolution per prime, reconstruction)"},
@@ -642,44 +816,11 @@ def run_exact(args, world, rank, local):
         out["e2e"] = {"value": round(batch * world * 1000.0 / ems, 1), "unit": "conv/s", "ms_per_step": round(ems, 3),
                       "h2d_bytes_per_step": 2 * batch * N * 8, "d2h_bytes_per_step": batch * N * 8,
                       "entry": "conv_exact with torch copies from/to pinned host memory"}
-        if world == 1 and rank == 0:
-            import oracle
-            o = oracle.Oracle()
-            nb = min(batch, 64)
-            fn, gn = fh[:nb].numpy(), gh[:nb].numpy()
-            threads = os.cpu_count() or 1
-            stop = time.perf_counter() + args.cpu_seconds
-            lock = threading.Lock()
-            state = {"next": 0, "done": 0}
-            blk = 256
-
-            def worker():
-                while time.perf_counter() < stop:
-                    with lock:
-                        k = state["next"]
-                        state["next"] += 1
-                    pair, off = divmod(k * blk, N)
-                    idx = np.arange(off, off + blk, dtype=np.uint64)
-                    o.int_conv_sample(fn[pair % nb], gn[pair % nb], idx)
-                    with lock:
-                        state["done"] += blk
-
-            t0 = time.perf_counter()
-            ths = [threading.Thread(target=worker) for _ in range(threads)]
-            for t in ths:
-                t.start()
-            for t in ths:
-                t.join()
-            el = time.perf_counter() - t0
-            out["cpu_baseline"] = {"value": round(state["done"] / N / el, 4), "unit": "conv/s", "cores": threads,
-                                   "kind": "oracle",
-                                   "sample": f"exact Eq. 1 in 128-bit integers (oracle or_int_conv_sample) on "
-                                             f"{state['done']} output indices of the first {nb} pairs in {el:.1f} s"}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+        attach_cpu_baseline(out, "exact6", args, world, rank, full=False)
+    return out
 
 
-def run_uneven(args, world, rank, local):
+def measure_uneven(args, world, rank, local, sub=False):
     """10,000 convolutions of lengths 2^6..2^19 in one batch plan, replayed as
     a CUDA graph; every length class runs its fused kernel."""
     import numpy as np
@@ -696,11 +837,8 @@ def run_uneven(args, world, rank, local):
     g = inputs.uniform_mod_torch(M, total, seed, 1, device="cuda")
     h = torch.empty_like(f)
     triples = [(f[o:o + n], g[o:o + n], h[o:o + n]) for o, n in zip(offs.tolist(), lens.tolist())]
-    schedule = {}
-    if args.schedule and os.path.exists(args.schedule):
-        ntt.ntt_autotune_load(args.schedule)
-        schedule = {"loaded": args.schedule}
-    else:
+    if args.tune and not sub:
+        schedule = {}
         for k in range(15, 20):                      # split-path classes: autotune form and pairs per wave
             cnt = int((lens == (1 << k)).sum())
             if cnt:
@@ -708,6 +846,8 @@ def run_uneven(args, world, rank, local):
                 schedule[f"2^{k}"] = {"wave": t["wave"], "twist": bool(t["twist"])}
         if args.schedule:
             ntt.ntt_autotune_save(args.schedule)
+    else:
+        schedule = load_schedule(args, ntt)
     bp = ntt.BatchPlan(M, triples)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -729,50 +869,50 @@ def run_uneven(args, world, rank, local):
     alg_bytes = 12.0 * total
     L = np.log2(lens).astype(np.int64)
     modmul = float(np.sum(3 * (lens // 2) * L + lens))
-    alu_peak = torch.cuda.get_device_properties(local).multi_processor_count * IMAD_PER_SM_CLK * sm_max_mhz * 1e6 \
-        / SLOTS_PER_MODMUL / 1e9
+    alu_peak = alu_peak_gmodmul(local, sm_max_mhz)
     alu_ach = modmul / (ms * 1e-3) / 1e9
     out = {"metric": METRIC, "value": round(count * world * 1000.0 / ms, 1), "unit": "conv/s", "n_gpus": world,
            "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded counter-based)",
-           "config": {"workload": desc, "pairs": count, "elements": total, "m": M,
-                      "schedule_pairs_per_wave": schedule},
+           "config": config_of("conv4", args, world), "elements": total, "schedule": schedule,
            "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1),
                         "unit": "Gmodmul/s", "frac": round(alu_ach / alu_peak, 4), "traffic": None,
-                        "kernel": "all length classes of one step (graph replay)"},
+                        "kernel": "all length classes of one step (graph replay); the split classes' rows "
+                                  "(k_conv_cr<u32,14,14,·,1>) dominate"},
            "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / (ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
                             "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                             "peak_src": f"{peak_src} copy bandwidth"},
            "clocks": clk.summary(), "gpu_launches": launches}
-    # end to end: each step copies f and g in from pinned host memory (one
-    # copy each), replays the batch plan and copies h back
-    h_dev = h.clone()
-    fh, gh = f.cpu().pin_memory(), g.cpu().pin_memory()
-    hh = torch.empty_like(fh).pin_memory()
-    esteps = max(1, min(args.steps, 5))
-    for i in range(esteps + 1):
-        if i == 1:
-            torch.cuda.synchronize()
-            barrier(world)
-            t0 = time.perf_counter()
-        f.copy_(fh, non_blocking=True)
-        g.copy_(gh, non_blocking=True)
-        bp.exec_graph(stream)
-        hh.copy_(h, non_blocking=True)
-    torch.cuda.synchronize()
-    ems = max_over_ranks(world, (time.perf_counter() - t0) * 1000.0 / esteps)
-    out["e2e"] = {"value": round(count * world * 1000.0 / ems, 1), "unit": "conv/s", "ms_per_step": round(ems, 3),
-                  "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 4 * total,
-                  "entry": "ntt_batch_exec_graph between one host-to-device copy of f and of g (pinned) and one "
-                           "device-to-host copy of h",
-                  "bit_identical_to_device_path": bool(torch.equal(hh, h_dev.cpu()))}
+    if not args.quick:
+        # end to end: each step copies f and g in from pinned host memory (one
+        # copy each), replays the batch plan and copies h back
+        h_dev = h.clone()
+        fh, gh = f.cpu().pin_memory(), g.cpu().pin_memory()
+        hh = torch.empty_like(fh).pin_memory()
+        esteps = max(1, min(args.steps, 5))
+        for i in range(esteps + 1):
+            if i == 1:
+                torch.cuda.synchronize()
+                barrier(world)
+                t0 = time.perf_counter()
+            f.copy_(fh, non_blocking=True)
+            g.copy_(gh, non_blocking=True)
+            bp.exec_graph(stream)
+            hh.copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(world, (time.perf_counter() - t0) * 1000.0 / esteps)
+        out["e2e"] = {"value": round(count * world * 1000.0 / ems, 1), "unit": "conv/s", "ms_per_step": round(ems, 3),
+                      "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 4 * total,
+                      "entry": "ntt_batch_exec_graph between one host-to-device copy of f and of g (pinned) and one "
+                               "device-to-host copy of h",
+                      "bit_identical_to_device_path": bool(torch.equal(hh, h_dev.cpu()))}
+        del fh, gh, hh, h_dev
+        attach_cpu_baseline(out, "conv4", args, world, rank, full=not sub)
     bp.close()
-    attach_cpu_baseline(out, args, world, rank)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
-def run_serve(args, world, rank, local):
+def measure_serve(args, world, rank, local, sub=False):
     """Open-loop Poisson load on the convolution server: requests are
     submitted at their arrival times from pinned host buffers; latency is
     submit -> result back in host memory (p50/p99 from the server)."""
@@ -781,7 +921,7 @@ def run_serve(args, world, rank, local):
 
     from paper_1005_1497_gb300 import inputs, ntt
 
-    m, rate, duration = 70525124609, 20000.0, max(0.5, min(args.steps / 1000.0, 3.0))
+    m, rate, duration = M64, 20000.0, max(0.5, min(args.steps / 1000.0, 3.0))
     count = int(rate * duration)
     seed = 2000 + rank
     K = 512                                           # distinct request buffers, reused cyclically
@@ -836,8 +976,9 @@ def run_serve(args, world, rank, local):
            "steps": count, "warmup": min(K, 64), "ms_per_step": round(elapsed * 1000.0 / count, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
            "data": "synthetic (seeded counter-based; Poisson arrivals)",
-           "config": {"workload": WORKLOADS["serve5"][2], "offered_req_per_s": rate, "requests": count,
-                      "mean_N": round(mean_n, 1), "pool_bytes": 2 << 30, "streams": 4, "max_batch": 256},
+           "config": config_of("serve5", args, world),
+           "server_config": {"requests": count, "mean_N": round(mean_n, 1), "pool_bytes": 2 << 30, "streams": 4,
+                             "max_batch": 256},
            "latency_us": {"p50": round(stats["p50_us"], 1), "p99": round(stats["p99_us"], 1),
                           "mean": round(stats["mean_us"], 1), "max": round(stats["max_us"], 1)},
            "server": {k: stats[k] for k in ("completed", "rejected", "batches", "max_inflight_batches",
@@ -846,6 +987,8 @@ def run_serve(args, world, rank, local):
            "capacity": {"req_per_s": round(cap["completed"] / cap_elapsed, 1), "requests": ccount,
                         "in_flight": K, "p50_us": round(cap["p50_us"], 1), "p99_us": round(cap["p99_us"], 1),
                         "GBps_host_io": round(24.0 * mean_n * cap["completed"] / cap_elapsed / 1e9, 1)},
+           "roofline": {"bound": "latency", "note": "20k req/s of ~48k-word requests offer about 23 GB/s: the "
+                                                     "served path is latency-bound, its latency is the figure"},
            "clocks": clk.summary(), "gpu_launches": launches}
     # the serving rate is itself end to end: every request goes from host
     # memory to its result in host memory through ntt_server_submit
@@ -853,138 +996,79 @@ def run_serve(args, world, rank, local):
                   "d2h_bytes_per_step": round(8.0 * mean_n, 1),
                   "entry": "ntt_server_submit / ntt_server_wait on pinned host buffers (a step is one request; "
                            "mean bytes read and written across the host link)"}
-    attach_cpu_baseline(out, args, world, rank)
+    attach_cpu_baseline(out, "serve5", args, world, rank, full=not sub)
+    return out
+
+
+def attach_cpu_baseline(out, name, args, world, rank, full):
+    """The oracle on the workload's own pairs, rank 0 at N=1 only, within a
+    bounded budget (the full budget for the line's own workload, a quarter
+    of it for each attached workload)."""
+    if world != 1 or rank != 0:
+        return
+    out["cpu_baseline"] = cpu_baseline(name, args, args.cpu_seconds if full else args.cpu_seconds / 4, full)
+
+
+MEASURE = {"conv1": lambda *a, **k: measure_uniform("conv1", *a, **k),
+           "conv2": lambda *a, **k: measure_uniform("conv2", *a, **k),
+           "conv3": lambda *a, **k: measure_uniform("conv3", *a, **k),
+           "conv4": measure_uneven, "serve5": measure_serve, "exact6": measure_exact, "shift7": measure_shift}
+
+# keys of an attached workload's object
+SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "config", "roofline", "roofline_hbm", "clocks", "e2e",
+            "cpu_baseline", "gpu_launches", "latency_us", "capacity", "server", "schedule", "launch", "noalloc")
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    out = MEASURE[args.workload](args, world, rank, local)
+    if args.workload == "conv2" and not args.quick and not args.no_configs and args.log2n is None \
+            and args.batch is None:
+        configs = {}
+        for name in SUB_CONFIGS:
+            torch.cuda.empty_cache()
+            sub = MEASURE[name](args, world, rank, local, sub=True)
+            configs[name] = {k: sub[k] for k in SUB_KEYS if k in sub}
+        out["configs"] = configs
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # --------------------------------------------------------- reference arm
 
-def oracle_rate_mixed(pairs, budget_s: float):
-    """Time the oracle on sampled outputs of a list of pairs (f, g, m, kind):
-    kind "mod" is Eq. 1 modulo m (or_conv_sample), "int" the exact integer
-    convolution (or_int_conv_sample).  Every host thread takes blocks of
-    output indices round-robin over the pairs (8 on the first visit of a pair,
-    256 after), so that each pair is sampled however mixed the lengths; a
-    pair's time is its sampled seconds scaled by N / outputs (each output of
-    the oracle costs N products), and the rate is threads x pairs over the sum
-    of those times.  Returns (conv/s, threads, outputs, wall s)."""
-    import numpy as np
-
-    import oracle
-    o = oracle.Oracle()
-    threads = os.cpu_count() or 1
-    P = len(pairs)
-    stop = time.perf_counter() + budget_s
-    lock = threading.Lock()
-    nxt = [0]
-    cursor, spent, outs = [0] * P, [0.0] * P, [0] * P
-
-    def worker():
-        while True:
-            with lock:
-                k = nxt[0]
-                if k >= P and time.perf_counter() >= stop:
-                    return
-                nxt[0] += 1
-                i = k % P
-                f, g, m, kind = pairs[i]
-                N = f.shape[-1]
-                cnt = min(N, 8 if k < P else 256)
-                off = cursor[i]
-                cursor[i] = (off + cnt) % N
-            idx = ((off + np.arange(cnt, dtype=np.uint64)) % np.uint64(N)).astype(np.uint64)
-            t = time.perf_counter()
-            if kind == "int":
-                o.int_conv_sample(f, g, idx)
-            else:
-                o.conv_sample(f, g, m, idx)
-            dt = time.perf_counter() - t
-            with lock:
-                spent[i] += dt
-                outs[i] += cnt
-
-    t0 = time.perf_counter()
-    ths = [threading.Thread(target=worker) for _ in range(threads)]
-    for t in ths:
-        t.start()
-    for t in ths:
-        t.join()
-    el = time.perf_counter() - t0
-    est = sum(spent[i] * pairs[i][0].shape[-1] / outs[i] for i in range(P))
-    return threads * P / est, threads, sum(outs), el
-
-
-def reference_pairs(args):
-    """Up to 64 pairs of the workload, from the same seeded generators."""
-    import numpy as np
-
-    from paper_1005_1497_gb300 import inputs
-    w = args.workload
-    if w == "conv4":
-        lens = inputs.log_uniform_lengths(WORKLOADS["conv4"][0], 6, 19, seed=1000)[:64]
-        return [(*(a[0] for a in inputs.pairs(M, 1, int(n), seed=1000 + i)), M, "mod")
-                for i, n in enumerate(lens)], WORKLOADS[w][2], "conv/s"
-    if w == "serve5":
-        m64 = 70525124609
-        lens = inputs.log_uniform_lengths(512, 8, 18, seed=2000)[:64]
-        return [(*(a[0] for a in inputs.pairs(m64, 1, int(n), seed=2000 + i)), m64, "mod")
-                for i, n in enumerate(lens)], WORKLOADS[w][2], "req/s"
-    batch, L, desc = WORKLOADS[w]
-    if args.log2n is not None:
-        L = args.log2n
-    N = 1 << L
-    if w == "exact6":
-        amp = 1 << 15
-        out = []
-        for i in range(min(batch, 64)):
-            f = inputs.uniform_mod(2 * amp + 1, N, 1000 + i, 0, dtype=np.uint64).astype(np.int64) - amp
-            g = inputs.uniform_mod(2 * amp + 1, N, 1000 + i, 1, dtype=np.uint64).astype(np.int64) - amp
-            out.append((f, g, 0, "int"))
-        return out, desc, "conv/s"
-    m = 641 if w == "shift7" else M
-    f, g = inputs.pairs(m, min(batch, 64), N, seed=1000)
-    return [(f[i], g[i], m, "mod") for i in range(f.shape[0])], desc, "conv/s"
-
-
-def attach_cpu_baseline(out, args, world, rank):
-    """The oracle's rate on the workload's own pairs (every length of a mixed
-    workload sampled), rank 0 at N=1 only, within --cpu-seconds."""
-    if world != 1 or rank != 0:
-        return
-    pairs, _, unit = reference_pairs(args)
-    rate, thr, done, el = oracle_rate_mixed(pairs, args.cpu_seconds)
-    kind = "exact integer Eq. 1 (oracle or_int_conv_sample)" if pairs[0][3] == "int" else \
-        "direct Eq. 1 (oracle or_conv_sample)"
-    out["cpu_baseline"] = {"value": round(rate, 4), "unit": unit, "cores": thr, "kind": "oracle",
-                           "sample": f"{kind} on {done} output indices sampled from each of {len(pairs)} pairs of "
-                                     f"the workload in {el:.1f} s; each pair's time scaled to all N outputs"}
-
-
 def run_reference(args):
     """The oracle, as it stands, timed on the host cores on bounded samples of
-    the same workload (rank 0 only)."""
+    the same workload (rank 0 only): its radix-2 convolution on whole pairs,
+    threads over pairs (exact integer workloads: direct Eq. 1 on sampled
+    outputs)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    pairs, desc, unit = reference_pairs(args)
+    pairs, unit = reference_pairs(args.workload, args)
     per_step = max(1.0, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_rate_mixed(pairs, per_step / 4)
-    rates, total_out, thr = [], 0, 1
+        oracle_rate_mixed(pairs, per_step / 4, kind="fast")
+    rates, total, thr = [], 0, 1
     for _ in range(args.steps):
-        r, thr, done, _ = oracle_rate_mixed(pairs, per_step)
+        r, thr, done, _ = oracle_rate_mixed(pairs, per_step, kind="fast")
         rates.append(r)
-        total_out += done
+        total += done
     value = statistics.median(rates)
-    kind = "exact integer Eq. 1 in 128-bit integers" if pairs[0][3] == "int" else "direct Eq. 1"
-    sample = (f"{kind} on {total_out} output indices sampled from each of {len(pairs)} pairs of the workload, "
-              f"{per_step:.1f} s per step; each pair's time scaled from its sampled outputs to all N of them")
+    integer = pairs[0][3] == "int"
+    what = ("exact integer Eq. 1 in 128-bit integers on sampled outputs" if integer else
+            "the oracle's radix-2 convolution (or_fast_conv) on whole pairs, threads over pairs")
+    sample = (f"{what}: {total} {'outputs' if integer else 'pair convolutions'} over {len(pairs)} pairs of the "
+              f"workload, {per_step:.1f} s per step; rate = threads x pairs / sum of each pair's time")
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": unit, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 * per_step, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (oracle, __int128 products)",
            "data": "synthetic (seeded counter-based)",
-           "config": {"workload": desc, "form": "CPU oracle", "pairs_sampled": len(pairs)},
+           "config": config_of(args.workload, args, args.gpus),
            "cpu_baseline": {"value": round(value, 4), "unit": unit, "cores": thr, "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 4), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
