@@ -73,9 +73,9 @@ def parse(argv=None):
                     help="override log2 N of the uniform workloads (conv1/conv2/conv3 shapes), e.g. for profiling")
     ap.add_argument("--batch", type=int, default=None, help="override the number of pairs of the uniform workloads")
     ap.add_argument("--schedule", default=None,
-                    help="split-path schedule file: loaded if it exists (no autotuning), else written after tuning; "
-                         "default: the packaged GB300 schedule when present, else the plan's heuristic")
-    ap.add_argument("--tune", action="store_true", help="autotune the split-path classes before timing")
+                    help="schedule file to load (default: the packaged GB300 schedule when present, else the plans' "
+                         "heuristics); with --tune, the file the tuned schedule is written to")
+    ap.add_argument("--tune", action="store_true", help="autotune the split-path classes in this run instead")
     return ap.parse_args(argv)
 
 
@@ -244,8 +244,9 @@ def config_of(name: str, args, world: int = 1) -> dict:
 
 
 def load_schedule(args, ntt) -> dict:
-    """Split-path schedules: the file given (or the packaged GB300 one) when it
-    exists; none (the plan's heuristic) otherwise."""
+    """The autotuned schedules (split-path wave and form, whole-sequence
+    threads per block, persistent-launch membership): the file given, or the
+    packaged GB300 one, when it exists; none (the plans' heuristics) otherwise."""
     path = args.schedule if args.schedule else SCHEDULE
     if path and os.path.exists(path):
         ntt.ntt_autotune_load(path)
@@ -418,11 +419,11 @@ def measure_uniform(name, args, world, rank, local, sub=False):
                         "tuned_ms": round(t["ms"], 4), "heuristic_ms": round(t["default_ms"], 4)}
             if args.schedule:
                 ntt.ntt_autotune_save(args.schedule)
-        else:
-            schedule = load_schedule(args, ntt)
     plan = ntt.Plan(M, N)
     if plan.four_step:
         schedule.update({"pairs_per_wave": plan.wave, "twist_form": plan.twist})
+    else:
+        schedule.update({"threads_per_block": plan.block})
     # inputs from the shared seeded generator (computed on the device), resident in HBM
     seed = 1000 + rank
     f = inputs.uniform_mod_torch(M, batch * N, seed, 0, device="cuda").view(batch, N)
@@ -847,7 +848,7 @@ def measure_uneven(args, world, rank, local, sub=False):
         if args.schedule:
             ntt.ntt_autotune_save(args.schedule)
     else:
-        schedule = load_schedule(args, ntt)
+        schedule = {}
     bp = ntt.BatchPlan(M, triples)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -1022,8 +1023,11 @@ SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "config", "roofline", "roof
 def run_ours(args):
     import torch
 
+    from paper_1005_1497_gb300 import ntt
     world, rank, local = dist_setup()
+    sched = load_schedule(args, ntt) if not args.tune else {"loaded": None, "tuned": "in this run"}
     out = MEASURE[args.workload](args, world, rank, local)
+    out["schedule_file"] = sched
     if args.workload == "conv2" and not args.quick and not args.no_configs and args.log2n is None \
             and args.batch is None:
         configs = {}

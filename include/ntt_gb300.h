@@ -117,6 +117,9 @@ typedef struct {
     uint32_t wave;       /* pairs per scratch wave of the split path (0 if unused) */
     uint32_t twist;      /* 1 when the split path (convolutions and natural-order transforms) uses
                             the four-step twist form, 0 for row-dependent twiddles */
+    uint32_t block;      /* whole sequences: threads per block of the fused convolution kernel
+                            (512, or 256 below the longest whole length); 0 on the split path */
+    uint32_t reserved;
 } ntt_plan_info_t;
 
 /* Fill *info with the plan's parameters.  Errors: NTT_ERR_ARG. */
@@ -209,25 +212,41 @@ void ntt_batch_destroy(ntt_batch_t batch);
 /* -------------------------------------------------------------- autotuning */
 
 typedef struct {
-    uint32_t wave;          /* chosen pairs per scratch wave (split path) */
+    uint32_t wave;          /* split path: chosen pairs per scratch wave (0 for whole sequences) */
     uint32_t default_wave;  /* the heuristic choice (4 rows per SM, or 256 MB of scratch if more) */
-    uint32_t twist;         /* chosen form: 1 the four-step twist, 0 row-dependent twiddles */
+    uint32_t twist;         /* split path: chosen form, 1 the four-step twist, 0 row-dependent twiddles */
     uint32_t default_twist; /* the heuristic form */
     double ms;              /* time of one convolution call over `batch` pairs with the choice */
-    double default_ms;      /* the same with the heuristic wave and form (0 if not measured) */
+    double default_ms;      /* the same with the heuristic schedule (0 if not measured) */
+    uint32_t block;         /* whole sequences: chosen threads per block of the fused kernel */
+    uint32_t default_block; /* 512 */
+    uint32_t persist;       /* whole sequences: 1 when a batch plan should run the length inside its
+                               persistent launch, 0 as a launch of its own */
+    uint32_t default_persist;  /* 1 for lengths that fit one warp, else 0 */
+    double persist_ms;      /* a batch of `batch` pairs with the length in the persistent launch */
+    double own_launch_ms;   /* the same batch with the length as its own launch (0 if not measured) */
 } ntt_tune_result;
 
-/* Time the split path's candidate schedules -- both forms (the four-step
- * twist, or row-dependent twiddles) times the pairs per scratch wave
- * (powers of two, the heuristic, all pairs) -- for `batch` pairs of length
- * N modulo m on the current GPU, and record the fastest for (GPU name, word
- * size, log2 N); plans created afterwards use it.  Lengths that fit one
- * block have no schedule to choose and return the default.  Synchronous;
- * allocates its own buffers.  Errors: as ntt_plan, NTT_ERR_OOM, NTT_ERR_CUDA. */
+/* Time the candidate schedules of `batch` pairs of length N modulo m on the
+ * current GPU and record the fastest for (GPU name, word size, log2 N);
+ * plans and batch plans created afterwards use it.
+ *  - Split path (N above one block): both forms (the four-step twist, or
+ *    row-dependent twiddles) times the pairs per scratch wave (powers of
+ *    two, the heuristic, all pairs).
+ *  - Whole sequences: the fused kernel's threads per block (512, or 256 --
+ *    half the rows and shared memory per block, two blocks per SM -- except
+ *    at the longest whole length), and for lengths above one warp's
+ *    (column/row lengths) whether a batch plan runs them inside its single
+ *    persistent launch or as a launch of their own.
+ * Synchronous; allocates its own buffers.  Errors: as ntt_plan,
+ * NTT_ERR_OOM, NTT_ERR_CUDA. */
 ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tune_result *out);
 
 /* Write / read the recorded schedules as JSON ({"schedules": [...]}, one
- * entry per GPU name, word size and log2 N).  Errors: NTT_ERR_ARG. */
+ * entry per GPU name, word size and log2 N, with the fields wave, twist,
+ * block, persist and ms; entries without block / persist take the
+ * defaults).  Loading adds to (and overrides) the recorded table.
+ * Errors: NTT_ERR_ARG. */
 ntt_status ntt_autotune_save(const char *path);
 ntt_status ntt_autotune_load(const char *path);
 

@@ -22,26 +22,40 @@ int Launch<W>::rows_per_block(int LR)
 }
 
 // Whole sequences: rows that fit one warp run the warp-level kernel; longer
-// ones (up to one block) the column/row kernel.
-template <typename W, int L, int SRC>
-static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t st)
+// ones (up to one block) the column/row kernel.  BLK threads per block.
+template <typename W, int L, int SRC, int BLK>
+static cudaError_t launch_conv_full_blk(const RowArgs<W> &a, int grid, cudaStream_t st)
 {
     constexpr int RW = Arith<W>::RB + 5;
     if constexpr (L <= RW) {
-        constexpr size_t smem = TwBytes<W, L>::v + RowShape<W, L, L>::smem(2);
-        static const cudaError_t init = ensure_smem(k_conv_fused<W, L, SRC>, smem);
+        constexpr size_t smem = TwBytes<W, L>::v + RowShape<W, L, L, BLK>::smem(2);
+        static const cudaError_t init = ensure_smem(k_conv_fused<W, L, SRC, BLK>, smem);
         if (init != cudaSuccess) return init;
-        k_conv_fused<W, L, SRC><<<grid, BLOCK, smem, st>>>(a);
+        k_conv_fused<W, L, SRC, BLK><<<grid, BLK, smem, st>>>(a);
         return launched();
-    } else if constexpr (L <= LRMax<W>::v) {
-        constexpr size_t smem = CRShape<W, L>::smem;
-        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, L, SRC>, smem);
+    } else if constexpr (L <= LRMax<W>::v && (BLK == BLOCK || L < LRMax<W>::v)) {
+        constexpr size_t smem = CRShape<W, L, L, BLK>::smem;
+        static const cudaError_t init = ensure_smem(k_conv_cr<W, L, L, SRC, 0, BLK>, smem);
         if (init != cudaSuccess) return init;
-        k_conv_cr<W, L, L, SRC><<<grid, BLOCK, smem, st>>>(a);
+        k_conv_cr<W, L, L, SRC, 0, BLK><<<grid, BLK, smem, st>>>(a);
         return launched();
     } else {
         return cudaErrorInvalidValue;
     }
+}
+
+template <typename W, int L, int SRC>
+static cudaError_t launch_conv_full(const RowArgs<W> &a, int grid, cudaStream_t st, int block)
+{
+    if (block == BLOCK_HALF) return launch_conv_full_blk<W, L, SRC, BLOCK_HALF>(a, grid, st);
+    return launch_conv_full_blk<W, L, SRC, BLOCK>(a, grid, st);
+}
+
+template <typename W>
+bool Launch<W>::block_ok(int L, int block)
+{
+    if (block == BLOCK) return L >= 0 && L <= LRMAX;
+    return block == BLOCK_HALF && L >= 0 && L < LRMAX;
 }
 
 template <typename W, int L>
@@ -100,11 +114,11 @@ static cudaError_t launch_exact(const RowArgs<W> &a, const ExactArgs &e, int gri
 }
 
 template <typename W>
-int Launch<W>::pairs_per_block(int L)
+int Launch<W>::pairs_per_block(int L, int block)
 {
     const int RW = Arith<W>::RB + 5;
-    if (L <= RW) return rows_per_block(L);
-    return BLOCK / (32 << (L - RW));
+    if (L <= RW) return rows_per_block(L) * block / BLOCK;
+    return block / (32 << (L - RW));
 }
 
 // Rows of a convolution's split path.  Untwisted: one row of 2^LR of the
@@ -237,16 +251,19 @@ static cudaError_t launch_bitrev(const W *src, W *dst, long long batch, const Mo
     }
 
 template <typename W>
-cudaError_t Launch<W>::conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st)
+template <int SRC>
+cudaError_t Launch<W>::conv_full_src(int L, const RowArgs<W> &a, int grid, cudaStream_t st, int block)
 {
-    if (src == 1) {
-#define C1(X) launch_conv_full<W, X, 1>(a, grid, st)
-        NTT_SWITCH_L(C1)
-#undef C1
-    }
-#define C0(X) launch_conv_full<W, X, 0>(a, grid, st)
-    NTT_SWITCH_L(C0)
-#undef C0
+#define C(X) launch_conv_full<W, X, SRC>(a, grid, st, block)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W>
+cudaError_t Launch<W>::conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st, int block)
+{
+    if (!block_ok(L, block)) return cudaErrorInvalidValue;
+    return src == 1 ? conv_full_src<1>(L, a, grid, st, block) : conv_full_src<0>(L, a, grid, st, block);
 }
 
 template <typename W>

@@ -90,6 +90,7 @@ struct ntt_plan_s {
     int LR = 0;
     uint32_t wave = 0;                 // pairs per scratch wave (split path)
     bool twist = false;                // split path form: the four-step twist (else row-dependent twiddles)
+    int block = ntt::BLOCK;            // whole sequences: threads per block of the fused kernel
     void *scratch = nullptr;           // 2 * wave * N words
     void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
     void *pd = nullptr;                // one column pass: the twist factor of element x, at x (the diagonal)
@@ -168,6 +169,12 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
     const int lrmax = word == 32 ? Launch<uint32_t>::LRMAX : Launch<uint64_t>::LRMAX;
     p->split = L > lrmax;
     p->LR = p->split ? lrmax : L;
+    ntt_schedule_t sched;
+    const bool tuned = ntt_tuned_schedule(word, L, &sched);
+    if (!p->split && tuned) {
+        const bool ok = word == 32 ? Launch<uint32_t>::block_ok(L, sched.block) : Launch<uint64_t>::block_ok(L, sched.block);
+        if (ok) p->block = sched.block;
+    }
 
     // Twiddles z_i = w^{brv_{L-1}(i)}, i < N/2, with w^e = 2^{e N_Max / N}
     // generated by doubling modulo m (shift and conditional subtraction).
@@ -204,9 +211,8 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
         // GB300 (64 pairs of 2^19 words, the whole of the uneven batch's
         // classes), where the scratch is a small part of the 280 GB.
         const uint64_t rows_per_pair = 1ull << (L - p->LR);
-        uint32_t tuned_wave = 0;
-        int tuned_twist = -1;
-        ntt_tuned_schedule(word, L, &tuned_wave, &tuned_twist);      // autotuned schedule, if any
+        const uint32_t tuned_wave = tuned ? sched.wave : 0u;      // autotuned schedule, if any
+        const int tuned_twist = tuned ? sched.twist : -1;
         uint64_t wave = tuned_wave;
         if (wave == 0)
             wave = std::max<uint64_t>((uint64_t)p->nsm * 4 / rows_per_pair, (256ull << 20) / (2 * (uint64_t)N * elt));
@@ -280,6 +286,7 @@ extern "C" ntt_status ntt_plan_get_info(ntt_plan_t p, ntt_plan_info_t *info)
     info->omega = p->omega; info->n_inv = p->n_inv; info->word_bits = (uint32_t)p->word;
     info->four_step = p->split ? 1u : 0u; info->wave = p->wave;
     info->twist = p->split && p->twist ? 1u : 0u;
+    info->block = p->split ? 0u : (uint32_t)p->block;
     return NTT_OK;
 }
 
@@ -291,10 +298,12 @@ template <typename W> static const ModC<W> &modc(ntt_plan_t p);
 template <> const ModC<uint32_t> &modc<uint32_t>(ntt_plan_t p) { return p->c32; }
 template <> const ModC<uint64_t> &modc<uint64_t>(ntt_plan_t p) { return p->c64; }
 
-static int row_grid(int nsm, long long rows, int per_block)
+// Persistent grid: as many blocks as the SMs hold at once (`per_sm` each),
+// fewer when the rows run out.
+static int row_grid(int nsm, long long rows, int per_block, int per_sm = 1)
 {
     long long blocks = (rows + per_block - 1) / per_block;
-    if (blocks > nsm) blocks = nsm;
+    if (blocks > (long long)nsm * per_sm) blocks = (long long)nsm * per_sm;
     return (int)(blocks > 0 ? blocks : 1);
 }
 
@@ -311,7 +320,8 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     const int mode = descs ? 1 : 0;
     if (!p->split) {
         RowArgs<W> a{f, g, h, descs, batch, pair0, tw, c};
-        return Launch<W>::conv_full(p->L, mode, a, row_grid(p->nsm, batch, Launch<W>::pairs_per_block(p->L)), st);
+        const int grid = row_grid(p->nsm, batch, Launch<W>::pairs_per_block(p->L, p->block), ntt::BLOCK / p->block);
+        return Launch<W>::conv_full(p->L, mode, a, grid, st, p->block);
     }
     const long long N = p->N;
     for (long long w0 = 0; w0 < batch; w0 += wave) {
@@ -527,6 +537,14 @@ int ntt_plan_log2(ntt_plan_t p) { return p ? p->L : -1; }
 
 int ntt_plan_device(ntt_plan_t p) { return p ? p->device : -1; }
 
+bool ntt_plan_set_block(ntt_plan_t p, int block)
+{
+    if (!p || p->split) return false;
+    const bool ok = p->word == 32 ? Launch<uint32_t>::block_ok(p->L, block) : Launch<uint64_t>::block_ok(p->L, block);
+    if (ok) p->block = block;
+    return ok;
+}
+
 ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs, long long count, void *scratch, uint32_t wave,
                           cudaStream_t st)
 {
@@ -566,16 +584,20 @@ ntt_status ntt_launch_exact(ntt_plan_t p, bool garner, const void *f64, const vo
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "exact fused launch");
 }
 
-// Longest length a batch plan folds into its persistent launch: the
-// one-warp lengths by default (their bodies share one kernel without
-// spilling); NTT_PERSIST_LMAX raises it to every whole-sequence length.
-int ntt_persist_lmax(int word_bits)
+// Whether a batch plan runs the whole-sequence length 2^L inside its one
+// persistent launch: always for the one-warp lengths (their bodies share one
+// kernel without spilling); for the column/row lengths when the autotuned
+// schedule says so, or when NTT_PERSIST_LMAX (a log2 length) reaches L.
+bool ntt_persist_class(int word_bits, int L)
 {
     const int rw = word_bits == 32 ? ntt::Arith<uint32_t>::RB + 5 : ntt::Arith<uint64_t>::RB + 5;
     const int lr = word_bits == 32 ? ntt::LRMax<uint32_t>::v : ntt::LRMax<uint64_t>::v;
-    const char *e = getenv("NTT_PERSIST_LMAX");
-    int v = e ? atoi(e) : rw;
-    return v <= rw ? rw : lr;
+    if (L <= rw) return true;
+    if (L > lr) return false;
+    if (const char *e = getenv("NTT_PERSIST_LMAX"))
+        if (atoi(e) >= L) return true;
+    ntt_schedule_t s;
+    return ntt_tuned_schedule(word_bits, L, &s) && s.persist != 0;
 }
 
 size_t ntt_full_smem(int word_bits, int log2N)

@@ -32,6 +32,10 @@ ntt_status ntt_cached_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     auto it = g_plan_cache.find({m, N});
     if (it != g_plan_cache.end()) {
+        // a schedule tuned or loaded since the plan was made applies to it too
+        ntt_schedule_t s;
+        if (ntt_tuned_schedule(ntt_plan_word_bits(it->second), ntt_plan_log2(it->second), &s))
+            ntt_plan_set_block(it->second, s.block);
         *out = it->second;
         return NTT_OK;
     }
@@ -153,12 +157,11 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
     // Longer lengths keep their own launches, spread over streams 1..K-1 by
     // longest-processing-time.
     const int lrmax = b->word == 32 ? ntt::LRMax<uint32_t>::v : ntt::LRMax<uint64_t>::v;
-    const int plmax = ntt_persist_lmax(b->word);
     std::vector<ntt::WorkItem> items;
     b->persist_plans.assign(lrmax + 1, nullptr);
     size_t nsplit = 0;             // classes with their own launches
     for (auto &c : b->classes) {
-        if (c.L > plmax) { ++nsplit; continue; }
+        if (!ntt_persist_class(b->word, c.L)) { ++nsplit; continue; }
         b->persist_lmax = std::max(b->persist_lmax, c.L);
         c.stream = -1;                                   // runs inside the persistent launch
         const int ppb = b->word == 32 ? ntt::Launch<uint32_t>::pairs_per_block(c.L) : ntt::Launch<uint64_t>::pairs_per_block(c.L);

@@ -34,9 +34,17 @@ ntt_status ntt_conv_descs(ntt_plan_t p, const void *descs_dev, long long count, 
 // split-path scratch (wave pairs of 2 N words); scratch unused when N fits one block.
 ntt_status ntt_conv_with_scratch(ntt_plan_t p, const void *f, const void *g, void *h, long long batch,
                                  void *scratch, uint32_t wave, cudaStream_t st, int twist = -1);   // twist: -1 the plan's form, 0 / 1 forced
-// Tuned pairs per scratch wave for (word size, log2 N) on the current GPU, 0 if untuned.
-// the autotuned split-path schedule for (this GPU, word size, log2 N); false if none
-bool ntt_tuned_schedule(int word_bits, int log2N, uint32_t *wave, int *twist);
+// The autotuned schedule of (this GPU, word size, log2 N); false if none.
+struct ntt_schedule_t {
+    uint32_t wave;          // split path: pairs per scratch wave
+    int twist;              // split path: 1 the four-step twist form, 0 row-dependent twiddles
+    int block;              // whole sequences: threads per block of the fused kernel
+    int persist;            // whole sequences: 1 when a batch plan runs the length in its persistent launch
+};
+bool ntt_tuned_schedule(int word_bits, int log2N, ntt_schedule_t *out);
+// Threads per block of a whole-sequence plan's fused kernel (the autotuner's
+// trial setting); false if the length has no such choice.
+bool ntt_plan_set_block(ntt_plan_t p, int block);
 // Device twiddle table of a plan, and its arithmetic constants (ModC<W> of
 // the plan's word size copied to out, `bytes` bytes).
 // One persistent launch of the whole-sequence fused bodies over a work list
@@ -44,7 +52,7 @@ bool ntt_tuned_schedule(int word_bits, int log2N, uint32_t *wave, int *twist);
 ntt_status ntt_launch_persistent(int word_bits, const void *descs, const void *items, int nitems, int *counter,
                                  const ntt_plan_t *plans, int lmax, int grid, size_t smem, cudaStream_t st);   // plans: indexed by log2 N, null where absent
 size_t ntt_full_smem(int word_bits, int log2N);
-int ntt_persist_lmax(int word_bits);
+bool ntt_persist_class(int word_bits, int L);
 // the exact convolution's fused launch of one prime (32-bit plans of whole
 // sequences); exact_args: an ntt::ExactArgs
 ntt_status ntt_launch_exact(ntt_plan_t p, bool garner, const void *f64, const void *g64, void *h, const void *exact_args,

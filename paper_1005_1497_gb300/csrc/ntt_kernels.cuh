@@ -7,7 +7,13 @@
 
 namespace ntt {
 
-constexpr int BLOCK = 512;                 // threads of every row-kernel block
+constexpr int BLOCK = 512;                 // threads of every row-kernel block (default)
+// The whole-sequence fused kernels also come with BLK = 256: half the rows
+// in flight and half the shared memory per block, so two blocks share an SM
+// and pass through their barrier-separated phases independently; the
+// autotuner picks per length (BLOCK for the longest whole length, whose
+// rows need 512 threads).
+constexpr int BLOCK_HALF = 256;
 
 template <typename W> struct LRMax;        // longest row one block transforms
 template <> struct LRMax<uint32_t> { static constexpr int v = 14; };
@@ -42,10 +48,10 @@ struct TwBytes {
     static constexpr size_t v = ((size_t)pairs * 2 * sizeof(W) + 15) / 16 * 16;
 };
 
-template <typename W, int L, int LR>
+template <typename W, int L, int LR, int BLK = BLOCK>
 struct RowShape {
     using G = Geo<W, LR>;
-    static constexpr int GPC = BLOCK / G::T;   // rows in flight per block
+    static constexpr int GPC = BLK / G::T;     // rows in flight per block
     static constexpr size_t smem(int ns) { return (size_t)GPC * ns * G::ROWP * sizeof(W); }
 };
 
@@ -166,10 +172,10 @@ __device__ __forceinline__ void conv_fused_body(const RowArgs<W> &a, long long b
     }
 }
 
-template <typename W, int L, int SRC>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_fused(const __grid_constant__ RowArgs<W> a)
+template <typename W, int L, int SRC, int BLK = BLOCK>
+__global__ void __launch_bounds__(BLK, BLOCK / BLK) k_conv_fused(const __grid_constant__ RowArgs<W> a)
 {
-    constexpr int GPC = RowShape<W, L, L>::GPC;
+    constexpr int GPC = RowShape<W, L, L, BLK>::GPC;
     conv_fused_body<W, L, SRC>(a, (long long)blockIdx.x * GPC, (long long)gridDim.x * GPC);
 }
 
@@ -321,14 +327,15 @@ __device__ __forceinline__ void cold_all(W (&v)[RR], uint32_t ptau, const W *__r
     }
 }
 
-template <typename W, int L, int LROW = L>
+template <typename W, int L, int LROW = L, int BLK = BLOCK>
 struct CRShape {
     static constexpr int RW = Arith<W>::RB + 5;
     static constexpr int LC = LROW - RW;                    // column bits inside one row
     static constexpr int RC = 1 << LC;
     using GR = Geo<W, RW>;
     static constexpr int TPP = 32 * RC;                     // threads per row
-    static constexpr int PPC = BLOCK / TPP;                 // rows per block
+    static constexpr int PPC = BLK / TPP;                   // rows per block
+    static_assert(PPC >= 1, "a row needs more threads than the block has");
     static constexpr int CPT = (1 << RW) / TPP;             // columns per thread
     // shared twiddles: the whole table (whole sequences) or only the entries
     // below 2^(LROW-1) that the inverse levels inside a row read (split rows)
@@ -345,11 +352,11 @@ struct CRShape {
 // Rows [base + row group, end) by steps of stride; end is a.nrows unless ITEM.
 // OUT 0: canonical at <-x>_N (a whole convolution); OUT 1: lazy residues in
 // natural order (a row of a convolution's split path, after the twist).
-template <typename W, int L, int LROW, int SRC, bool ITEM = false, int OUT = 0, class X = NoExact>
+template <typename W, int L, int LROW, int SRC, bool ITEM = false, int OUT = 0, class X = NoExact, int BLK = BLOCK>
 __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base, long long stride, long long end = 0,
                                              const ExactArgs *xa = nullptr)
 {
-    using SH = CRShape<W, L, LROW>;
+    using SH = CRShape<W, L, LROW, BLK>;
     using GR = typename SH::GR;
     constexpr int RW = SH::RW, LC = SH::LC, RC = SH::RC, TPP = SH::TPP, PPC = SH::PPC, CPT = SH::CPT;
     constexpr int R = GR::R;
@@ -510,11 +517,11 @@ __device__ __forceinline__ void conv_cr_body(const RowArgs<W> &a, long long base
     }
 }
 
-template <typename W, int L, int LROW, int SRC, int OUT = 0>
-__global__ void __launch_bounds__(BLOCK, 1) k_conv_cr(const __grid_constant__ RowArgs<W> a)
+template <typename W, int L, int LROW, int SRC, int OUT = 0, int BLK = BLOCK>
+__global__ void __launch_bounds__(BLK, BLOCK / BLK) k_conv_cr(const __grid_constant__ RowArgs<W> a)
 {
-    constexpr int PPC = CRShape<W, L, LROW>::PPC;
-    conv_cr_body<W, L, LROW, SRC, false, OUT>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC);
+    constexpr int PPC = CRShape<W, L, LROW, BLK>::PPC;
+    conv_cr_body<W, L, LROW, SRC, false, OUT, NoExact, BLK>(a, (long long)blockIdx.x * PPC, (long long)gridDim.x * PPC);
 }
 
 // The exact convolution's fused launches (whole sequences, contiguous):

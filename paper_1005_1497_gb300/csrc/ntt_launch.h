@@ -13,10 +13,16 @@ template <typename W> struct Launch {
     static constexpr int LMAX = 20;            // split path: LMAX - LRMAX column bits, in two passes above 5
     // rows transformed concurrently by one block of the row kernels
     static int rows_per_block(int LR);
-    // pairs in flight per block of the whole-sequence fused kernels
-    static int pairs_per_block(int L);
+    // pairs in flight per block of the whole-sequence fused kernels with
+    // `block` threads per block (BLOCK, or BLOCK_HALF below LRMAX)
+    static int pairs_per_block(int L, int block = BLOCK);
+    // whether the whole-sequence fused kernels of length 2^L come with `block` threads
+    static bool block_ok(int L, int block);
     // whole-sequence fused convolution (L <= LRMAX); src 0 = contiguous, 1 = descriptors
-    static cudaError_t conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st);
+    static cudaError_t conv_full(int L, int src, const RowArgs<W> &a, int grid, cudaStream_t st, int block = BLOCK);
+    // (one source mode; instantiated in separate translation units)
+    template <int SRC>
+    static cudaError_t conv_full_src(int L, const RowArgs<W> &a, int grid, cudaStream_t st, int block);
     // split path pieces (LRMAX < L <= LMAX); cols_fwd / cols_inv run one or
     // two column passes
     // (twisted: the four-step twist form, see the twist in ntt_kernels.cuh)

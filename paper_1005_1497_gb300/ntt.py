@@ -73,7 +73,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64), ("N", ctypes.c_uint32), ("log2N", ctypes.c_uint32),
                 ("n_max", ctypes.c_uint64), ("omega", ctypes.c_uint64), ("n_inv", ctypes.c_uint64),
                 ("word_bits", ctypes.c_uint32), ("four_step", ctypes.c_uint32), ("wave", ctypes.c_uint32),
-                ("twist", ctypes.c_uint32)]
+                ("twist", ctypes.c_uint32), ("block", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 EXACT_MAX_PRIMES = 4
@@ -142,6 +142,7 @@ class Plan:
         self.n_max, self.omega, self.n_inv = int(info.n_max), int(info.omega), int(info.n_inv)
         self.word_bits, self.four_step, self.wave = int(info.word_bits), bool(info.four_step), int(info.wave)
         self.twist = bool(info.twist)
+        self.block = int(info.block)
         self.dtype = _DT[self.word_bits][0]
 
     def close(self):
@@ -444,15 +445,20 @@ class Server:
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("wave", ctypes.c_uint32), ("default_wave", ctypes.c_uint32), ("twist", ctypes.c_uint32),
-                ("default_twist", ctypes.c_uint32), ("ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("default_twist", ctypes.c_uint32), ("ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("block", ctypes.c_uint32), ("default_block", ctypes.c_uint32), ("persist", ctypes.c_uint32),
+                ("default_persist", ctypes.c_uint32), ("persist_ms", ctypes.c_double),
+                ("own_launch_ms", ctypes.c_double)]
 
 
 def ntt_autotune(m: int, N: int, batch: int) -> dict:
-    """Pick the split path's form and pairs-per-wave for (m, N) and `batch` pairs on this GPU."""
+    """``ntt_autotune``: measure and record the schedule of (m, N) for `batch`
+    pairs on this GPU -- the split path's form and pairs per wave, or a whole
+    length's threads per block and whether batch plans run it inside their
+    persistent launch."""
     r = TuneResult()
     _check(lib().ntt_autotune(m, N, batch, ctypes.byref(r)), "ntt_autotune")
-    return {"wave": r.wave, "default_wave": r.default_wave, "twist": r.twist, "default_twist": r.default_twist,
-            "ms": r.ms, "default_ms": r.default_ms}
+    return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
 
 def ntt_autotune_save(path: str):

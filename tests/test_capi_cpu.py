@@ -129,3 +129,31 @@ def test_launch_counter_needs_no_gpu(ntt):
     a = ntt.launch_count()
     assert isinstance(a, int) and a >= 0
     assert ntt.launch_count() >= a
+
+
+def test_schedule_file_roundtrip_without_a_gpu(ntt, tmp_path):
+    """ntt_autotune_load / _save on the host: entries of the current format and
+    older entries without block / persist (which take the defaults) are read,
+    malformed ones are skipped, and saving writes every knob back."""
+    src = tmp_path / "in.json"
+    src.write_text('{"schedules": [\n'
+                   '  {"gpu": "Some GPU", "word_bits": 32, "log2N": 12, "wave": 0, "twist": 1, "block": 256, '
+                   '"persist": 1, "ms": 0.5},\n'
+                   '  {"gpu": "Some GPU", "word_bits": 32, "log2N": 17, "wave": 12, "twist": 0, "ms": 0.25},\n'
+                   '  {"gpu": "Some GPU", "word_bits": 64, "log2N": 9, "wave": 0, "twist": 1, "ms": 0.1},\n'
+                   '  {"gpu": "Some GPU", "word_bits": 32, "log2N": 13, "wave": 0, "twist": 1, "block": 300, '
+                   '"persist": 0, "ms": 1.0}\n'
+                   ']}\n')
+    ntt.ntt_autotune_load(str(src))
+    out = tmp_path / "out.json"
+    ntt.ntt_autotune_save(str(out))
+    rows = {(r["word_bits"], r["log2N"]): r for r in
+            (__import__("json").loads(ln.strip().rstrip(",")) for ln in open(out) if '"gpu"' in ln)}
+    assert set(rows) >= {(32, 12), (32, 17), (64, 9)} and (32, 13) not in rows     # block 300 is not a choice
+    assert (rows[(32, 12)]["block"], rows[(32, 12)]["persist"]) == (256, 1)
+    assert (rows[(32, 17)]["wave"], rows[(32, 17)]["twist"], rows[(32, 17)]["block"]) == (12, 0, 512)
+    assert rows[(32, 17)]["persist"] == 0 and rows[(64, 9)]["persist"] == 1       # defaults: one-warp lengths persist
+    with pytest.raises(ntt.NttError):
+        bad = tmp_path / "bad.json"
+        bad.write_text('{"schedules": []}\n')
+        ntt.ntt_autotune_load(str(bad))
