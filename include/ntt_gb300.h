@@ -219,7 +219,7 @@ typedef struct {
     double ms;              /* time of one convolution call over `batch` pairs with the choice */
     double default_ms;      /* the same with the heuristic schedule (0 if not measured) */
     uint32_t block;         /* whole sequences: chosen threads per block of the fused kernel */
-    uint32_t default_block; /* 512 */
+    uint32_t default_block; /* the untuned choice: 256 for column/row lengths below the longest, else 512 */
     uint32_t persist;       /* whole sequences: 1 when a batch plan should run the length inside its
                                persistent launch, 0 as a launch of its own */
     uint32_t default_persist;  /* 1 for lengths that fit one warp, else 0 */

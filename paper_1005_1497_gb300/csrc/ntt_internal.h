@@ -45,6 +45,8 @@ bool ntt_tuned_schedule(int word_bits, int log2N, ntt_schedule_t *out);
 // Threads per block of a whole-sequence plan's fused kernel (the autotuner's
 // trial setting); false if the length has no such choice.
 bool ntt_plan_set_block(ntt_plan_t p, int block);
+// The untuned threads per block of the whole-sequence fused kernel of length 2^L.
+int ntt_default_block(int word_bits, int L);
 // Device twiddle table of a plan, and its arithmetic constants (ModC<W> of
 // the plan's word size copied to out, `bytes` bytes).
 // One persistent launch of the whole-sequence fused bodies over a work list

@@ -88,7 +88,7 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
     const int rw = word == 32 ? ntt::Arith<uint32_t>::RB + 5 : ntt::Arith<uint64_t>::RB + 5;
     out->default_wave = out->wave = info.wave;
     out->default_twist = out->twist = info.twist;
-    out->default_block = info.four_step ? 0u : (uint32_t)ntt::BLOCK;
+    out->default_block = info.four_step ? 0u : (uint32_t)ntt_default_block(word, L);
     out->block = info.block;
     out->default_persist = (!info.four_step && L <= rw) ? 1u : 0u;
     out->persist = out->default_persist;
@@ -113,7 +113,9 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    ntt_schedule_t best_s{info.wave, (int)info.twist, (int)info.block, (int)out->default_persist};
+    // (split lengths keep the whole-sequence defaults in their entry)
+    ntt_schedule_t best_s{info.wave, (int)info.twist, info.four_step ? ntt::BLOCK : (int)info.block,
+                          (int)out->default_persist};
     double best = 1e30, dflt = 0;
 
     if (info.four_step) {
@@ -140,7 +142,7 @@ extern "C" ntt_status ntt_autotune(uint64_t m, uint32_t N, size_t batch, ntt_tun
         for (int blk : {ntt::BLOCK, ntt::BLOCK_HALF}) {
             if (!ntt_plan_set_block(p, blk)) continue;
             const double t = time_ms(st, e0, e1, 5, [&] { return conv_circular(p, f, g, h, batch, (ntt_stream_t)st); });
-            if (blk == ntt::BLOCK) dflt = t;
+            if (blk == (int)out->default_block) dflt = t;
             if (t < best) { best = t; best_s.block = blk; }
         }
         // column/row lengths: inside a batch plan's persistent launch, or a
@@ -238,6 +240,7 @@ extern "C" ntt_status ntt_autotune_load(const char *path)
         json_int(line, "twist", &twist);
         json_int(line, "block", &block);
         json_int(line, "persist", &persist);
+        if (block == 0) block = ntt::BLOCK;          // (entries of split lengths may carry 0: no choice)
         if (const char *mq = strstr(line, "\"ms\": ")) sscanf(mq + 6, "%lf", &ms);
         if ((word != 32 && word != 64) || L < 0 || L > 31 || wave < 0 || wave > 0xffffffffll) continue;
         if ((twist != 0 && twist != 1) || (block != ntt::BLOCK && block != ntt::BLOCK_HALF)) continue;
