@@ -46,13 +46,15 @@ def test_autotune_reports_block_and_persist_for_a_whole_length(tmp_path):
     assert len(rows) == 3 and all('"block": ' in ln and '"persist": ' in ln for ln in rows)
 
 
-# a schedule whose every choice differs from the defaults where it can
+# a schedule whose every choice differs from the defaults where it can (one-warp
+# lengths in half blocks, column/row lengths in full ones, all of them in the
+# persistent launch; split lengths in waves of 3 pairs, row-dependent twiddles)
 def _schedule(name):
     rows = []
     for word, rw, lr, lmax in ((32, 10, 14, 19), (64, 9, 13, 20)):
         for L in range(0, lr + 1):
             rows.append({"gpu": name, "word_bits": word, "log2N": L, "wave": 0, "twist": 1,
-                         "block": 256 if L < lr else 512, "persist": 1, "ms": 1.0})
+                         "block": 256 if L <= rw else 512, "persist": 1, "ms": 1.0})
         for L in range(lr + 1, lmax + 1):
             rows.append({"gpu": name, "word_bits": word, "log2N": L, "wave": 3, "twist": 0, "block": 512,
                          "persist": 0, "ms": 1.0})
@@ -81,13 +83,13 @@ def test_multi_knob_schedule_roundtrip_and_parity(tmp_path):
         def ref(f, g, m, N):
             w = o.root(m, N)
             return np.stack([o.fast_conv(f[i], g[i], m, w) for i in range(f.shape[0])])
-        for m, word, Ls, lr in (({M}, 32, [0, 1, 5, 6, 10, 11, 12, 13, 14, 16], 14),
-                                ({M64}, 64, [0, 3, 9, 10, 11, 12, 13, 15], 13)):
+        for m, word, Ls, rw, lr in (({M}, 32, [0, 1, 5, 6, 10, 11, 12, 13, 14, 16], 10, 14),
+                                    ({M64}, 64, [0, 3, 9, 10, 11, 12, 13, 15], 9, 13)):
             for L in Ls:
                 N = 1 << L
                 p = ntt.Plan(m, N)
                 if L <= lr:
-                    assert p.block == (256 if L < lr else 512), (m, L, p.block)
+                    assert p.block == (256 if L <= rw else 512), (m, L, p.block)
                 else:
                     assert p.wave == 3 and not p.twist, (m, L, p.wave, p.twist)
                 batch = 7 if L < 12 else 5
