@@ -71,7 +71,10 @@ def parse(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle samples")
     ap.add_argument("--log2n", type=int, default=None,
                     help="override log2 N of the uniform workloads (conv1/conv2/conv3 shapes), e.g. for profiling")
-    ap.add_argument("--batch", type=int, default=None, help="override the number of pairs of the uniform workloads")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="override the number of pairs of the uniform workloads and of the uneven batch")
+    ap.add_argument("--m64", action="store_true",
+                    help="uniform workloads modulo the 64-bit-word prime 70525124609 (uint64), e.g. for profiling")
     ap.add_argument("--schedule", default=None,
                     help="schedule file to load (default: the packaged GB300 schedule when present, else the plans' "
                          "heuristics); with --tune, the file the tuned schedule is written to")
@@ -213,10 +216,11 @@ def traffic_from_profile(kernel_tag: str):
 def uniform_shape(name: str, args):
     """(batch, log2 N, description) of a uniform workload, with the overrides."""
     batch, L, desc = WORKLOADS[name]
-    if name in ("conv1", "conv2", "conv3") and (args.log2n is not None or args.batch is not None):
+    if name in ("conv1", "conv2", "conv3") and (args.log2n is not None or args.batch is not None or args.m64):
         L = args.log2n if args.log2n is not None else L
         batch = args.batch if args.batch is not None else batch
-        desc = f"uniform batch: {batch} pairs x N=2^{L}, m=13631489, uint32 (override)"
+        word = "m=70525124609, uint64" if args.m64 else "m=13631489, uint32"
+        desc = f"uniform batch: {batch} pairs x N=2^{L}, {word} (override)"
     return batch, L, desc
 
 
@@ -226,12 +230,14 @@ def config_of(name: str, args, world: int = 1) -> dict:
     if name in ("conv1", "conv2", "conv3"):
         batch, L, desc = uniform_shape(name, args)
         big = 8 * batch * (1 << L) > (129 << 20)
-        return {"workload": desc, "batch_per_gpu": batch, "N": 1 << L, "m": M,
+        return {"workload": desc, "batch_per_gpu": batch, "N": 1 << L, "m": M64 if args.m64 else M,
                 "l2": "inputs larger than L2; no flush" if big else
                       "inputs smaller than L2: every step rereads them from L2 (no flush)",
                 "parallelism": par}
     if name == "conv4":
-        return {"workload": WORKLOADS[name][2], "pairs": WORKLOADS[name][0], "m": M,
+        return {"workload": WORKLOADS[name][2] if args.batch is None else
+                f"uneven batch: {args.batch} pairs, N = 2^k with k uniform on {{6..19}}, m=13631489, uint32 (override)",
+                "pairs": args.batch or WORKLOADS[name][0], "m": M,
                 "l2": "inputs larger than L2 (6 GB of f+g); no flush", "parallelism": par}
     if name == "serve5":
         return {"workload": WORKLOADS[name][2], "offered_req_per_s": 20000.0, "m": M64, "parallelism": par}
@@ -342,7 +348,7 @@ def reference_pairs(name: str, args, cap: int = 64):
 
     from paper_1005_1497_gb300 import inputs
     if name == "conv4":
-        lens = inputs.log_uniform_lengths(WORKLOADS["conv4"][0], 6, 19, seed=1000)[:cap]
+        lens = inputs.log_uniform_lengths(args.batch or WORKLOADS["conv4"][0], 6, 19, seed=1000)[:cap]
         return [(*(a[0] for a in inputs.pairs(M, 1, int(n), seed=1000 + i)), M, "mod")
                 for i, n in enumerate(lens)], "conv/s"
     if name == "serve5":
@@ -363,8 +369,9 @@ def reference_pairs(name: str, args, cap: int = 64):
         f, g = inputs.pairs(641, min(batch, cap), 1 << L, seed=1000)
         return [(f[i], g[i], 641, "mod") for i in range(f.shape[0])], "conv/s"
     batch, L, _ = uniform_shape(name, args)
-    f, g = inputs.pairs(M, min(batch, cap), 1 << L, seed=1000)
-    return [(f[i], g[i], M, "mod") for i in range(f.shape[0])], "conv/s"
+    m = M64 if args.m64 else M
+    f, g = inputs.pairs(m, min(batch, cap), 1 << L, seed=1000, dtype=np.uint64)
+    return [(f[i], g[i], m, "mod") for i in range(f.shape[0])], "conv/s"
 
 
 def cpu_baseline(name: str, args, budget_s: float, full: bool) -> dict:
@@ -411,23 +418,26 @@ def measure_uniform(name, args, world, rank, local, sub=False):
 
     batch, L, desc = uniform_shape(name, args)
     N = 1 << L
+    m = M64 if args.m64 else M
+    wb = 8 if args.m64 else 4                                     # bytes per word
+    tdt = torch.int64 if args.m64 else torch.int32
     schedule = {}
-    if L > 14:                                                    # split path: form and pairs per wave
+    if L > (13 if args.m64 else 14):                              # split path: form and pairs per wave
         if args.tune and not sub:
-            t = ntt.ntt_autotune(M, N, batch)
+            t = ntt.ntt_autotune(m, N, batch)
             schedule = {"tuned": {k: t[k] for k in ("wave", "twist", "default_wave", "default_twist")},
                         "tuned_ms": round(t["ms"], 4), "heuristic_ms": round(t["default_ms"], 4)}
             if args.schedule:
                 ntt.ntt_autotune_save(args.schedule)
-    plan = ntt.Plan(M, N)
+    plan = ntt.Plan(m, N)
     if plan.four_step:
         schedule.update({"pairs_per_wave": plan.wave, "twist_form": plan.twist})
     else:
         schedule.update({"threads_per_block": plan.block})
     # inputs from the shared seeded generator (computed on the device), resident in HBM
     seed = 1000 + rank
-    f = inputs.uniform_mod_torch(M, batch * N, seed, 0, device="cuda").view(batch, N)
-    g = inputs.uniform_mod_torch(M, batch * N, seed, 1, device="cuda").view(batch, N)
+    f = inputs.uniform_mod_torch(m, batch * N, seed, 0, device="cuda", dtype=tdt).view(batch, N)
+    g = inputs.uniform_mod_torch(m, batch * N, seed, 1, device="cuda", dtype=tdt).view(batch, N)
     h = torch.empty_like(f)
     stream = torch.cuda.current_stream()
 
@@ -484,7 +494,7 @@ def measure_uniform(name, args, world, rank, local, sub=False):
     # roofline: the fused kernel (one launch per step when N fits one block),
     # or the split path's three kernels per wave, rows dominating
     hbm_peak, sm_max_mhz, peak_src = peaks()
-    alg_bytes = 12.0 * N * batch                                 # f, g in, h out (uint32)
+    alg_bytes = 3.0 * wb * N * batch                              # f, g in, h out
     modmul = batch * (3 * (N // 2) * L + N)                      # butterfly products + pointwise
     launch_ms = ms / launches_per_step
     alu_peak = alu_peak_gmodmul(local, sm_max_mhz)
@@ -494,17 +504,17 @@ def measure_uniform(name, args, world, rank, local, sub=False):
         kernel_tag = None
         kernel = ("split path, per wave k_cols_fwd + k_conv_cr<u32,14,14,0,1> (rows: 2^(L-14) whole length-2^14 "
                   "convolutions per pair, the dominant kernel) + k_cols_inv")
-    elif L > 10:
-        kernel_tag = f"k_conv_cr_u32_L{L}_{batch}x{N}"
-        kernel = f"k_conv_cr<u32,{L},{L},0,0> (fused, column/row form)"
+    elif L > (9 if args.m64 else 10):
+        kernel_tag = None if args.m64 else f"k_conv_cr_u32_L{L}_{batch}x{N}"
+        kernel = f"k_conv_cr<u{8 * wb},{L},{L},0,0,{plan.block}> (fused, column/row form)"
     else:
         kernel_tag = None
-        kernel = f"k_conv_fused<u32,{L},0> (fused, one warp per sequence)"
+        kernel = f"k_conv_fused<u{8 * wb},{L},0,{plan.block}> (fused, one warp per sequence)"
     traffic = traffic_from_profile(kernel_tag) if kernel_tag else None
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "conv/s", "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded counter-based uniform residues in [0,m))",
+        "vs_baseline": None, "dtype": f"u{8 * wb}", "data": "synthetic (seeded counter-based uniform residues in [0,m))",
         "config": config_of(name, args, world),
         "roofline": {"bound": "alu", "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
                      "frac": round(alu_ach / alu_peak, 4), "traffic": traffic,
@@ -547,7 +557,7 @@ def measure_uniform(name, args, world, rank, local, sub=False):
         del X
 
         # plain form: one launch per butterfly stage over the whole batch
-        work = torch.empty((2 * batch, N), dtype=torch.int32, device="cuda")
+        work = torch.empty((2 * batch, N), dtype=tdt, device="cuda")
         h2 = torch.empty_like(f)
         for _ in range(max(args.warmup, 1)):
             ntt.conv_circular_plain(plan, f, g, out=h2, work=work, stream=stream)
@@ -582,7 +592,7 @@ def measure_uniform(name, args, world, rank, local, sub=False):
         torch.cuda.synchronize()
         ems = max_over_ranks(world, (time.perf_counter() - t0) * 1000.0 / esteps)
         out["e2e"] = {"value": round(pairs_total * 1000.0 / ems, 1), "unit": "conv/s", "ms_per_step": round(ems, 3),
-                      "h2d_bytes_per_step": 2 * batch * N * 4, "d2h_bytes_per_step": batch * N * 4,
+                      "h2d_bytes_per_step": 2 * batch * N * wb, "d2h_bytes_per_step": batch * N * wb,
                       "entry": "conv_circular_host (pinned host buffers, chunked copy/compute overlap)",
                       "bit_identical_to_device_path": bool(torch.equal(hh, h.cpu()))}
         # the host link alone, for the same bytes (plain copies, untimed
@@ -609,10 +619,10 @@ def measure_uniform(name, args, world, rank, local, sub=False):
             torch.cuda.synchronize()
             return (time.perf_counter() - t) * 1000.0 / reps
 
-        if 3 * batch * N * 4 >= (64 << 20):      # (a few KB per step measure launch latency, not the link)
+        if 3 * batch * N * wb >= (64 << 20):     # (a few KB per step measure launch latency, not the link)
             in_ms, out_ms, both_ms = copies_ms(True, False), copies_ms(False, True), copies_ms(True, True)
-            out["e2e"]["host_link"] = {"h2d_GBps": round(2 * batch * N * 4 / (in_ms * 1e-3) / 1e9, 1),
-                                       "d2h_GBps": round(batch * N * 4 / (out_ms * 1e-3) / 1e9, 1),
+            out["e2e"]["host_link"] = {"h2d_GBps": round(2 * batch * N * wb / (in_ms * 1e-3) / 1e9, 1),
+                                       "d2h_GBps": round(batch * N * wb / (out_ms * 1e-3) / 1e9, 1),
                                        "both_directions_ms": round(both_ms, 3),
                                        "frac": round(both_ms / ems, 4),
                                        "note": "frac = the step's copies alone (both directions at once) / e2e step time"}
@@ -829,7 +839,7 @@ def measure_uneven(args, world, rank, local, sub=False):
 
     from paper_1005_1497_gb300 import inputs, ntt
 
-    count, _, desc = WORKLOADS["conv4"]
+    count = args.batch or WORKLOADS["conv4"][0]
     seed = 1000 + rank
     lens = inputs.log_uniform_lengths(count, 6, 19, seed=seed)
     offs = np.concatenate([[0], np.cumsum(lens)[:-1]])
