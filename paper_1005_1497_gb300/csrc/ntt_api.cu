@@ -94,7 +94,6 @@ struct ntt_plan_s {
     void *scratch = nullptr;           // 2 * wave * N words
     void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
     void *pd = nullptr;                // one column pass: the twist factor of element x, at x (the diagonal)
-    uint32_t *pdm = nullptr;           // the same diagonal as 4-byte Montgomery forms w 2^32 mod m (32-bit words)
     void *pwl = nullptr;               // split path: (w^(s l), quotient) at s 32 + l, s < 2^(L - LR), l < 32
     int nsm = 1;
     int device = 0;
@@ -136,7 +135,6 @@ extern "C" void ntt_plan_destroy(ntt_plan_t p)
     cudaFree(p->scratch);
     cudaFree(p->pw);
     cudaFree(p->pd);
-    cudaFree(p->pdm);
     cudaFree(p->pwl);
     cudaFree(p->counter);
     cudaFree(p->stage);
@@ -256,23 +254,8 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
                 const size_t e = (sk * t) % N;
                 memcpy(&dg[2 * x * elt], &tab[2 * e * elt], 2 * elt);
             }
-            if (word == 64) {
-                if (!ntt::dev_alloc(&p->pd, dg.size())) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twist diagonal");
-                CUDA_TRY(cudaMemcpy(p->pd, dg.data(), dg.size(), cudaMemcpyHostToDevice), "ntt_plan: upload twist diagonal");
-            } else {
-                // 32-bit words: 4-byte Montgomery forms instead of (factor,
-                // quotient) pairs -- half the column passes' reads of the
-                // diagonal, for a Montgomery product in place of a Shoup
-                // product (measured 1.0% faster at 64 x 2^19 on GB300)
-                std::vector<uint32_t> dm(N);
-                for (size_t x = 0; x < N; ++x) {
-                    uint32_t z;
-                    memcpy(&z, &dg[2 * x * elt], 4);
-                    dm[x] = (uint32_t)nt::shl_mod(z, 32, m);
-                }
-                if (!ntt::dev_alloc(&p->pdm, N * 4)) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twist diagonal");
-                CUDA_TRY(cudaMemcpy(p->pdm, dm.data(), N * 4, cudaMemcpyHostToDevice), "ntt_plan: upload twist diagonal");
-            }
+            if (!ntt::dev_alloc(&p->pd, dg.size())) return ntt_fail(NTT_ERR_OOM, "ntt_plan: twist diagonal");
+            CUDA_TRY(cudaMemcpy(p->pd, dg.data(), dg.size(), cudaMemcpyHostToDevice), "ntt_plan: upload twist diagonal");
         }
         const size_t ns = (size_t)1 << (L - p->LR);
         std::vector<unsigned char> lt(2 * ns * 32 * elt);
@@ -345,7 +328,7 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     for (long long w0 = 0; w0 < batch; w0 += wave) {
         const long long np = std::min<long long>(wave, batch - w0);
         ColArgs<W> ca{f, g, descs, scratch, scratch + (size_t)wave * N, h, np, pair0 + w0, tw, c, (const W *)p->pw,
-                      (const W *)p->pwl, (const W *)p->pd, p->pdm};
+                      (const W *)p->pwl, (const W *)p->pd};
         cudaError_t e = Launch<W>::cols_fwd(p->L, 2, mode, tw_form, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);
@@ -376,7 +359,7 @@ static cudaError_t ntt_dispatch(ntt_plan_t p, const W *x, W *y, long long batch,
         // or row-dependent twiddles; both leave the same tree order
         const bool twisted = p->twist;
         ColArgs<W> ca{x, nullptr, nullptr, scratch, nullptr, nullptr, np, w0, tw, c, (const W *)p->pw,
-                      (const W *)p->pwl, (const W *)p->pd, p->pdm};
+                      (const W *)p->pwl, (const W *)p->pd};
         cudaError_t e = Launch<W>::cols_fwd(p->L, 1, 0, twisted, ca, st);
         if (e != cudaSuccess) return e;
         const long long rows = np << (p->L - p->LR);

@@ -134,16 +134,6 @@ __device__ __forceinline__ void gs_bfly_one(W &a, W &b, const ModC<W> &c)
     b = d2 < d ? d2 : d;
 }
 
-// Montgomery product v z~ 2^-32 mod m in [0, 2m) for any v < 2^32 and z~ < m:
-// with z~ = z 2^32 mod m (a twiddle stored in Montgomery form) it is v z mod m.
-template <typename W>
-__device__ __forceinline__ uint32_t mont32(uint32_t v, uint32_t zt, const ModC<W> &c)
-{
-    const uint32_t lo = v * zt;
-    const uint32_t q = lo * (uint32_t)c.mneg;
-    return __umulhi(v, zt) + __umulhi(q, (uint32_t)c.m) + (lo != 0u ? 1u : 0u);
-}
-
 // Pointwise product F G N^{-1} mod m in [0, 2m): Shoup by N^{-1} 2^B, then a
 // Montgomery reduction of the double-word product.
 __device__ __forceinline__ uint32_t pointwise(uint32_t F, uint32_t G, const ModC<uint32_t> &c)

@@ -698,8 +698,7 @@ template <typename W> struct ColArgs {
     ModC<W> c;
     const W *pw;        // convolutions: (w^e, Shoup quotient) pairs, e < N (the twist)
     const W *pwl;       // (w^(s l), quotient) at s 32 + l, s < 2^(L-LR), l < 32
-    const W *pd;        // one column pass, 64-bit words: (w^(brv(k) t), quotient) at x = t + k 2^LR
-    const uint32_t *pdm;   // one column pass, 32-bit words: the same factors as w 2^32 mod m (Montgomery form)
+    const W *pd;        // one column pass: (w^(brv(k) t), quotient) at x = t + k 2^LR
 };
 
 // The four-step twist, one of the two forms of the split path of
@@ -717,10 +716,8 @@ template <typename W> struct ColArgs {
 // in [0, 2m).
 //
 // With one column pass the factor of element x = t + k 2^LR depends on x
-// alone (not on the pair), so the plan stores it at x: for 32-bit words as
-// its Montgomery form w 2^32 mod m (ColArgs::pdm, 4 bytes, one Montgomery
-// product), for 64-bit words as (factor, Shoup quotient) (ColArgs::pd, one
-// vector load and one Shoup product) -- coalesced and L2-resident either way.
+// alone (not on the pair), so the plan stores it at x (ColArgs::pd): one
+// coalesced, L2-resident vector load and one Shoup product per element.
 // With two column passes (k_cols_mid_*) it is split as w^(s t0) w^(s l),
 // t = t0 + l, l = t mod 32 (the lane): the first is the same for a warp (one
 // broadcast load), the second comes from a small lane table (s, l) ->
@@ -853,9 +850,10 @@ __global__ void __launch_bounds__(256, (TWIST && NS == 2 && sizeof(W) == 4) ? 3 
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             const uint32_t x = col + ((uint32_t)k << LR);
-            const uint32_t zt = __ldg(a.pdm + x);
-            df[x] = csub<W>(mont32(vf[k], zt, a.c), a.c.m);
-            dg[x] = csub<W>(mont32(vg[k], zt, a.c), a.c.m);
+            W z, zp;
+            ld_pair_g<W>(a.pd + 2 * (size_t)x, z, zp);
+            df[x] = csub<W>(shoup<W>(vf[k], z, zp, a.c.m), a.c.m);
+            dg[x] = csub<W>(shoup<W>(vg[k], z, zp, a.c.m), a.c.m);
         }
     } else {
 #pragma unroll 1
@@ -866,11 +864,7 @@ __global__ void __launch_bounds__(256, (TWIST && NS == 2 && sizeof(W) == 4) ? 3 
 #pragma unroll
             for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
             col_fwd_levels<W, L, LR, L - LR - 1>(v, a.tw, a.c);
-            if constexpr (TWIST && sizeof(W) == 4) {
-#pragma unroll
-                for (int k = 0; k < RC; ++k)
-                    v[k] = csub<W>((W)mont32((uint32_t)v[k], __ldg(a.pdm + col + ((uint32_t)k << LR)), a.c), a.c.m);
-            } else if constexpr (TWIST) {
+            if constexpr (TWIST) {
 #pragma unroll
                 for (int k = 0; k < RC; ++k) {
                     W z, zp;
@@ -908,10 +902,7 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
     W v[RC];
 #pragma unroll
     for (int k = 0; k < RC; ++k) v[k] = src[col + ((uint32_t)k << LR)];
-    if constexpr (TWIST && sizeof(W) == 4) {
-#pragma unroll
-        for (int k = 0; k < RC; ++k) v[k] = (W)mont32((uint32_t)v[k], __ldg(a.pdm + col + ((uint32_t)k << LR)), a.c);
-    } else if constexpr (TWIST) {
+    if constexpr (TWIST) {
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             W z, zp;
