@@ -886,8 +886,12 @@ __global__ void __launch_bounds__(256, (TWIST && NS == 2 && sizeof(W) == 4) ? 3 
 // x = c + k 2^LR): node twiddles k >> (J + 1), the same for every column.
 // Inputs < 2m; then the output stage: index <-x>_N, canonical residue.
 // DST 0: contiguous out; 1: descriptor h.
+// (32-bit words, contiguous output: at most 48 registers, five blocks per SM
+// for the loads in flight -- measured 1.7% faster for 64 x 2^19 on GB300;
+// the descriptor-output form spills at that bound and keeps its registers)
 template <typename W, int L, int LR, int DST, bool TWIST>
-__global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArgs<W> a)
+__global__ void __launch_bounds__(256, (DST == 0 && sizeof(W) == 4) ? 5 : 1)
+    k_cols_inv(const __grid_constant__ ColArgs<W> a)
 {
     constexpr int LC = L - LR, RC = 1 << LC;
     constexpr uint32_t N = 1u << L;
