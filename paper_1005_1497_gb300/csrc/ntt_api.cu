@@ -147,6 +147,7 @@ extern "C" void ntt_plan_destroy(ntt_plan_t p)
 
 extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
 {
+    ntt::Trace tr("ntt_plan");
     if (!out) return ntt_fail(NTT_ERR_ARG, "ntt_plan: out is NULL");
     *out = nullptr;
     if (m < 3 || !nt::is_prime(m)) return ntt_fail(NTT_ERR_MODULUS, "ntt_plan: m=%llu is not an odd prime", (unsigned long long)m);
@@ -375,6 +376,7 @@ static cudaError_t ntt_dispatch(ntt_plan_t p, const W *x, W *y, long long batch,
 
 extern "C" ntt_status ntt_forward(ntt_plan_t p, const void *x, void *X, size_t batch, ntt_stream_t stream)
 {
+    ntt::Trace tr("ntt_forward");
     if (!p || !x || !X || batch == 0) return ntt_fail(NTT_ERR_ARG, "ntt_forward: invalid argument");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = p->word == 32 ? ntt_dispatch<uint32_t>(p, (const uint32_t *)x, (uint32_t *)X, (long long)batch, false, st)
@@ -384,6 +386,7 @@ extern "C" ntt_status ntt_forward(ntt_plan_t p, const void *x, void *X, size_t b
 
 extern "C" ntt_status ntt_inverse(ntt_plan_t p, const void *X, void *x, size_t batch, ntt_stream_t stream)
 {
+    ntt::Trace tr("ntt_inverse");
     if (!p || !x || !X || batch == 0) return ntt_fail(NTT_ERR_ARG, "ntt_inverse: invalid argument");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = p->word == 32 ? ntt_dispatch<uint32_t>(p, (const uint32_t *)X, (uint32_t *)x, (long long)batch, true, st)
@@ -394,6 +397,7 @@ extern "C" ntt_status ntt_inverse(ntt_plan_t p, const void *X, void *x, size_t b
 extern "C" ntt_status conv_circular(ntt_plan_t p, const void *f, const void *g, void *h, size_t batch,
                                     ntt_stream_t stream)
 {
+    ntt::Trace tr("conv_circular");
     if (!p || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular: invalid argument");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = p->word == 32
@@ -452,6 +456,7 @@ static const void *host_device_address(const void *p)
 extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void *g, void *h, size_t batch,
                                          ntt_stream_t stream)
 {
+    ntt::Trace tr("conv_circular_host");
     if (!p || !f || !g || !h || batch == 0) return ntt_fail(NTT_ERR_ARG, "conv_circular_host: invalid argument");
     const size_t elt = p->word / 8;
     const size_t seq = (size_t)p->N * elt;

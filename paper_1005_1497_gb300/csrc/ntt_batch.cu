@@ -98,6 +98,7 @@ extern "C" void ntt_batch_destroy(ntt_batch_t b)
 
 extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, size_t count, ntt_batch_t *out)
 {
+    ntt::Trace tr("ntt_batch_plan");
     if (!out || !descs || count == 0) return ntt_fail(NTT_ERR_ARG, "ntt_batch_plan: invalid argument");
     *out = nullptr;
     std::map<uint32_t, std::vector<size_t>> by_len;
@@ -207,6 +208,7 @@ extern "C" ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, siz
 
 extern "C" ntt_status ntt_batch_exec(ntt_batch_t b, ntt_stream_t stream)
 {
+    ntt::Trace tr("ntt_batch_exec");
     if (!b) return ntt_fail(NTT_ERR_ARG, "ntt_batch_exec: NULL batch");
     cudaStream_t user = (cudaStream_t)stream;
     if (cudaEventRecord(b->fork, user) != cudaSuccess) return ntt_fail(NTT_ERR_CUDA, "ntt_batch_exec: record");
@@ -234,6 +236,7 @@ extern "C" ntt_status ntt_batch_exec(ntt_batch_t b, ntt_stream_t stream)
 
 extern "C" ntt_status ntt_batch_exec_graph(ntt_batch_t b, ntt_stream_t stream)
 {
+    ntt::Trace tr("ntt_batch_exec_graph");
     if (!b) return ntt_fail(NTT_ERR_ARG, "ntt_batch_exec_graph: NULL batch");
     cudaStream_t user = (cudaStream_t)stream;
     if (!b->gexec) {

@@ -2,9 +2,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include "../../include/ntt_gb300.h"
 
 namespace ntt {
+// An NVTX range for the lifetime of the object: plan creation, dispatch,
+// batch execution and graph replay, and the server's batches show up as
+// named ranges in a profiler's timeline (NVTX does nothing when no tool is
+// attached).
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
+
 // cudaMalloc that leaves no error behind when it fails: the library checks
 // every launch with cudaGetLastError(), which would otherwise report the
 // failed allocation again at the next (good) launch of this thread.

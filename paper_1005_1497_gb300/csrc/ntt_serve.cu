@@ -244,6 +244,7 @@ static void server_loop(ntt_server_t s)
         // launches, outside the lock
         for (size_t i : to_launch) {
             Slot &slot = s->slots[i];
+            ntt::Trace tr("server batch");
             const ntt_status e = server_launch(s, slot, slot.reqs);
             if (e == NTT_OK) continue;
             std::lock_guard<std::mutex> lk(s->mu);

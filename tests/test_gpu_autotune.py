@@ -123,3 +123,31 @@ def test_multi_knob_schedule_roundtrip_and_parity(tmp_path):
     for r in saved:
         w = want[key(r)]
         assert (r["wave"], r["twist"], r["block"], r["persist"]) == (w["wave"], w["twist"], w["block"], w["persist"])
+
+
+def test_schedule_file_named_by_the_environment(tmp_path):
+    """NTT_SCHEDULE: the first plan of a process loads the named schedule file."""
+    need_gpu()
+    name = torch.cuda.get_device_name(0)
+    src = tmp_path / "env.json"
+    src.write_text('{"schedules": [\n  {"gpu": "%s", "word_bits": 32, "log2N": 12, "wave": 0, "twist": 1, '
+                   '"block": 512, "persist": 0, "ms": 1.0}\n]}\n' % name)
+    code = textwrap.dedent(f"""
+        import sys
+        import numpy as np
+        sys.path.insert(0, {ROOT!r}); sys.path.insert(0, {os.path.join(ROOT, "tests")!r})
+        import oracle
+        from paper_1005_1497_gb300 import ntt
+        from gpu_util import dev, host, pairs
+        p = ntt.Plan({M}, 1 << 12)
+        assert p.block == 512, p.block                   # the default below 2^14 is 256
+        f, g = pairs({M}, 3, 1 << 12, seed=55)
+        h = host(ntt.conv_circular(p, dev(f, 32), dev(g, 32)))
+        o = oracle.Oracle()
+        w = o.root({M}, 1 << 12)
+        assert all(np.array_equal(h[i], o.fast_conv(f[i], g[i], {M}, w)) for i in range(3))
+        print("ok")
+    """)
+    env = {**os.environ, "NTT_SCHEDULE": str(src)}
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, env=env)
+    assert res.returncode == 0 and "ok" in res.stdout, res.stdout + res.stderr
