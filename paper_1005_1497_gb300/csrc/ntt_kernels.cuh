@@ -886,12 +886,8 @@ __global__ void __launch_bounds__(256, (TWIST && NS == 2 && sizeof(W) == 4) ? 3 
 // x = c + k 2^LR): node twiddles k >> (J + 1), the same for every column.
 // Inputs < 2m; then the output stage: index <-x>_N, canonical residue.
 // DST 0: contiguous out; 1: descriptor h.
-// (32-bit words, contiguous output: at most 48 registers, five blocks per SM
-// for the loads in flight -- measured 1.7% faster for 64 x 2^19 on GB300;
-// the descriptor-output form spills at that bound and keeps its registers)
 template <typename W, int L, int LR, int DST, bool TWIST>
-__global__ void __launch_bounds__(256, (DST == 0 && sizeof(W) == 4) ? 5 : 1)
-    k_cols_inv(const __grid_constant__ ColArgs<W> a)
+__device__ __forceinline__ void cols_inv_body(const ColArgs<W> &a)
 {
     constexpr int LC = L - LR, RC = 1 << LC;
     constexpr uint32_t N = 1u << L;
@@ -922,6 +918,23 @@ __global__ void __launch_bounds__(256, (DST == 0 && sizeof(W) == 4) ? 5 : 1)
         const uint32_t x = col + ((uint32_t)k << LR);
         out[(N - x) & (N - 1u)] = csub<W>(v[k], a.c.m);
     }
+}
+
+template <typename W, int L, int LR, int DST, bool TWIST>
+__global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArgs<W> a)
+{
+    cols_inv_body<W, L, LR, DST, TWIST>(a);
+}
+
+// The same with at most 48 registers, five blocks per SM for the loads in
+// flight: used for 32-bit words with contiguous output and five column bits,
+// where the plain bound takes 56 registers (four blocks); measured 1.7%
+// faster for 64 x 2^19 on GB300.  (An explicit bound raises the register
+// count of the shorter and 64-bit forms instead, so they keep the plain one.)
+template <typename W, int L, int LR, bool TWIST>
+__global__ void __launch_bounds__(256, 5) k_cols_inv5(const __grid_constant__ ColArgs<W> a)
+{
+    cols_inv_body<W, L, LR, 0, TWIST>(a);
 }
 
 // Split path with more column bits than one thread holds (L - LR > 5):
