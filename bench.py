@@ -507,6 +507,9 @@ def measure_uniform(name, args, world, rank, local, sub=False):
     elif L > (9 if args.m64 else 10):
         kernel_tag = None if args.m64 else f"k_conv_cr_u32_L{L}_{batch}x{N}"
         kernel = f"k_conv_cr<u{8 * wb},{L},{L},0,0,{plan.block}> (fused, column/row form)"
+    elif batch <= plan.small_max:
+        kernel_tag = None
+        kernel = f"k_conv_small<u{8 * wb},{L}> (fused, one thread block per pair: a batch too small to fill the GPU)"
     else:
         kernel_tag = None
         kernel = f"k_conv_fused<u{8 * wb},{L},0,{plan.block}> (fused, one warp per sequence)"

@@ -119,7 +119,10 @@ typedef struct {
                             the four-step twist form, 0 for row-dependent twiddles */
     uint32_t block;      /* whole sequences: threads per block of the fused convolution kernel
                             (512, or 256 below the longest whole length); 0 on the split path */
-    uint32_t reserved;
+    uint32_t small_max;  /* lengths of one warp's row (2^10 for 32-bit words, 2^9 for 64-bit):
+                            conv_circular on contiguous pairs runs batches up to this size with one
+                            thread block per pair instead of one warp per pair (too few pairs to fill
+                            the GPU); 0 for longer lengths */
 } ntt_plan_info_t;
 
 /* Fill *info with the plan's parameters.  Errors: NTT_ERR_ARG. */

@@ -89,7 +89,8 @@ def _prune(keep) -> None:
 
 
 
-_KERNEL_SOURCES = ("csrc/ntt_core.cuh", "csrc/ntt_kernels.cuh", "csrc/ntt_exact.cuh", "csrc/launch_impl.cuh",
+_KERNEL_SOURCES = ("csrc/ntt_core.cuh", "csrc/ntt_kernels.cuh", "csrc/ntt_small.cuh", "csrc/ntt_exact.cuh",
+                   "csrc/launch_impl.cuh",
                    "csrc/ntt_launch.h", "../include/ntt_gb300.h")
 
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "ntt_launch.h"
+#include "ntt_small.cuh"
 
 namespace ntt {
 
@@ -258,6 +259,28 @@ template <int SRC>
 cudaError_t Launch<W>::conv_full_src(int L, const RowArgs<W> &a, int grid, cudaStream_t st, int block)
 {
 #define C(X) launch_conv_full<W, X, SRC>(a, grid, st, block)
+    NTT_SWITCH_L(C)
+#undef C
+}
+
+template <typename W, int L>
+static cudaError_t launch_conv_small(const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+    if constexpr (L <= Arith<W>::RB + 5) {
+        constexpr size_t smem = SmallShape<W, L>::smem;
+        static const cudaError_t init = ensure_smem(k_conv_small<W, L>, smem);
+        if (init != cudaSuccess) return init;
+        k_conv_small<W, L><<<grid, SMALL_THREADS, smem, st>>>(a);
+        return launched();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W>
+cudaError_t Launch<W>::conv_small(int L, const RowArgs<W> &a, int grid, cudaStream_t st)
+{
+#define C(X) launch_conv_small<W, X>(a, grid, st)
     NTT_SWITCH_L(C)
 #undef C
 }

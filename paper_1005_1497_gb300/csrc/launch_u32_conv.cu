@@ -6,4 +6,5 @@ template int Launch<uint32_t>::pairs_per_block(int, int);
 template bool Launch<uint32_t>::block_ok(int, int);
 template cudaError_t Launch<uint32_t>::conv_full(int, int, const RowArgs<uint32_t> &, int, cudaStream_t, int);
 template cudaError_t Launch<uint32_t>::conv_full_src<0>(int, const RowArgs<uint32_t> &, int, cudaStream_t, int);
+template cudaError_t Launch<uint32_t>::conv_small(int, const RowArgs<uint32_t> &, int, cudaStream_t);
 }  // namespace ntt

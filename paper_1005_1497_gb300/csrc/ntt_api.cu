@@ -91,6 +91,7 @@ struct ntt_plan_s {
     uint32_t wave = 0;                 // pairs per scratch wave (split path)
     bool twist = false;                // split path form: the four-step twist (else row-dependent twiddles)
     int block = ntt::BLOCK;            // whole sequences: threads per block of the fused kernel
+    long long small_max = 0;           // whole one-warp lengths: batches up to this run one block per pair
     void *scratch = nullptr;           // 2 * wave * N words
     void *pw = nullptr;                // split path: (w^e, Shoup quotient), e < N (the twist)
     void *pd = nullptr;                // one column pass: the twist factor of element x, at x (the diagonal)
@@ -118,6 +119,20 @@ static void fill_modc(ModC<W> &c, uint64_t m, uint64_t ninv)
     c.onep = (W)nt::shoup_quot(1, m, B);
     c.ninv = (W)ninv;
     c.ninvp = (W)nt::shoup_quot(ninv, m, B);
+}
+
+// Largest batch of a one-warp length (L <= RB + 5) that conv_circular runs
+// with one block per pair (k_conv_small) instead of one warp per pair.  The
+// one-warp kernels win once the batch fills the GPU: measured on GB300, the
+// crossover lies near 16 KB of input per SM (2^10, 32-bit words: 608 pairs;
+// 64-bit words at 2^9: between 608 and 1216), and beyond 32 pairs per SM the
+// block-per-pair kernel's idle threads at the shortest lengths cost more.
+static long long small_batch_max(int word, int L, int nsm)
+{
+    const int rw = word == 32 ? ntt::Arith<uint32_t>::RB + 5 : ntt::Arith<uint64_t>::RB + 5;
+    if (L > rw) return 0;
+    const long long by_bytes = (long long)nsm * 16384 / ((1LL << L) * (word / 8));
+    return std::max<long long>(1, std::min<long long>(by_bytes, (long long)nsm * 32));
 }
 
 static int num_sms()
@@ -171,6 +186,7 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
     p->split = L > lrmax;
     p->LR = p->split ? lrmax : L;
     if (!p->split) p->block = ntt_default_block(word, L);
+    if (!p->split) p->small_max = small_batch_max(word, L, p->nsm);
     ntt_schedule_t sched;
     const bool tuned = ntt_tuned_schedule(word, L, &sched);
     if (!p->split && tuned) {
@@ -289,6 +305,7 @@ extern "C" ntt_status ntt_plan_get_info(ntt_plan_t p, ntt_plan_info_t *info)
     info->four_step = p->split ? 1u : 0u; info->wave = p->wave;
     info->twist = p->split && p->twist ? 1u : 0u;
     info->block = p->split ? 0u : (uint32_t)p->block;
+    info->small_max = (uint32_t)std::min<long long>(p->small_max, 0xffffffffLL);
     return NTT_OK;
 }
 
@@ -322,6 +339,8 @@ static cudaError_t conv_dispatch(ntt_plan_t p, const W *f, const W *g, W *h, con
     const int mode = descs ? 1 : 0;
     if (!p->split) {
         RowArgs<W> a{f, g, h, descs, batch, pair0, tw, c};
+        if (mode == 0 && batch <= p->small_max)
+            return Launch<W>::conv_small(p->L, a, (int)std::min<long long>(batch, (long long)p->nsm * Launch<W>::SMALL_PER_SM), st);
         const int grid = row_grid(p->nsm, batch, Launch<W>::pairs_per_block(p->L, p->block), ntt::BLOCK / p->block);
         return Launch<W>::conv_full(p->L, mode, a, grid, st, p->block);
     }

@@ -23,6 +23,10 @@ template <typename W> struct Launch {
     // (one source mode; instantiated in separate translation units)
     template <int SRC>
     static cudaError_t conv_full_src(int L, const RowArgs<W> &a, int grid, cudaStream_t st, int block);
+    // one pair per block (k_conv_small) for the one-warp lengths (L <= RB + 5),
+    // contiguous pairs; grid blocks walk the pairs
+    static cudaError_t conv_small(int L, const RowArgs<W> &a, int grid, cudaStream_t st);
+    static constexpr int SMALL_PER_SM = 8;     // blocks of k_conv_small resident per SM (256 threads, <= 37 registers)
     // split path pieces (LRMAX < L <= LMAX); cols_fwd / cols_inv run one or
     // two column passes
     // (twisted: the four-step twist form, see the twist in ntt_kernels.cuh)

@@ -73,7 +73,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64), ("N", ctypes.c_uint32), ("log2N", ctypes.c_uint32),
                 ("n_max", ctypes.c_uint64), ("omega", ctypes.c_uint64), ("n_inv", ctypes.c_uint64),
                 ("word_bits", ctypes.c_uint32), ("four_step", ctypes.c_uint32), ("wave", ctypes.c_uint32),
-                ("twist", ctypes.c_uint32), ("block", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("twist", ctypes.c_uint32), ("block", ctypes.c_uint32), ("small_max", ctypes.c_uint32)]
 
 
 EXACT_MAX_PRIMES = 4
@@ -143,6 +143,7 @@ class Plan:
         self.word_bits, self.four_step, self.wave = int(info.word_bits), bool(info.four_step), int(info.wave)
         self.twist = bool(info.twist)
         self.block = int(info.block)
+        self.small_max = int(info.small_max)   # batches up to this run one block per pair
         self.dtype = _DT[self.word_bits][0]
 
     def close(self):
