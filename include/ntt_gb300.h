@@ -167,12 +167,14 @@ ntt_status conv_circular_plain(ntt_plan_t plan, const void *f_dev, const void *g
  * outbound copies) so that those steps of different chunks overlap.  Device
  * staging memory (4 slots x 3 chunks, about 200 MB at most) is allocated on
  * first use and kept by the plan.  With page-locked buffers (cudaHostAlloc /
- * cudaHostRegister), which the GPU can address over the C2C link, the
- * environment variable NTT_HOST_DIRECT=p (0..100) sends p percent of the
- * pairs through the kernels in place instead, for whole-sequence lengths
- * (default 0: measured slower than the copies).  Returns after h_host is
- * complete (synchronises `stream`).  Errors: NTT_ERR_ARG, NTT_ERR_OOM,
- * NTT_ERR_CUDA. */
+ * cudaHostRegister), which the GPU can address over the C2C link, and
+ * whole-sequence lengths, a batch whose f, g and h total at most 96 MB is
+ * instead read and written in place by the kernels (no copies: lower latency
+ * for small batches; larger batches are faster through the copy pipeline).
+ * The environment variable NTT_HOST_DIRECT=p (0..100) overrides that choice
+ * and sends p percent of the pairs in place, the rest through the copies.
+ * Returns after h_host is complete (synchronises `stream`).  Errors:
+ * NTT_ERR_ARG, NTT_ERR_OOM, NTT_ERR_CUDA. */
 ntt_status conv_circular_host(ntt_plan_t plan, const void *f_host, const void *g_host, void *h_host,
                               size_t batch, ntt_stream_t stream);
 

@@ -326,6 +326,26 @@ def test_host_buffers(ntt, orc, monkeypatch, direct):
         assert np.array_equal(hp.numpy().astype(np.uint64), want)
 
 
+def test_host_buffers_default_choice(ntt, orc, monkeypatch):
+    """Without NTT_HOST_DIRECT: a small page-locked batch goes in place, a
+    pageable one through the copies; both equal the device path and Eq. 1."""
+    monkeypatch.delenv("NTT_HOST_DIRECT", raising=False)
+    for L, batch in ((0, 3), (10, 1), (12, 5), (14, 2)):
+        N = 1 << L
+        plan = ntt.Plan(M, N)
+        f, g = pairs(M, batch, N, seed=820 + L)
+        ft = torch.from_numpy(f.astype(np.int32)).pin_memory()
+        gt = torch.from_numpy(g.astype(np.int32)).pin_memory()
+        ht = torch.empty_like(ft).pin_memory()
+        ntt.conv_circular_host(plan, ft, gt, ht)
+        want = host(ntt.conv_circular(plan, ft.cuda(), gt.cuda()))
+        assert np.array_equal(ht.numpy().astype(np.uint64), want), L
+        assert np.array_equal(want, ref_conv(orc, f, g, M, plan.omega)), L
+        hp = torch.empty_like(ft)
+        ntt.conv_circular_host(plan, ft.clone(), gt.clone(), hp)
+        assert np.array_equal(hp.numpy().astype(np.uint64), want), L
+
+
 def test_host_buffers_many_chunks(ntt, orc):
     """More chunks than the host pipeline has slots (1100 pairs of 2^14:
     four full chunks of 256 pairs and a ragged fifth), so slots are reused
