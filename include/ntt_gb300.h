@@ -203,9 +203,10 @@ ntt_status conv_batched(uint64_t m, const ntt_conv_desc *descs, size_t count, nt
  * executed. */
 ntt_status ntt_batch_plan(uint64_t m, const ntt_conv_desc *descs, size_t count, ntt_batch_t *out);
 
-/* Enqueue every convolution of the batch plan on `stream` (length classes
- * run on forked internal streams joined back into `stream`).  Capturable in
- * a CUDA graph. */
+/* Enqueue every convolution of the batch plan on `stream` (the persistent
+ * launch of the short lengths and the other length classes' launches run on
+ * two forked internal streams joined back into `stream`).  Capturable in a
+ * CUDA graph. */
 ntt_status ntt_batch_exec(ntt_batch_t batch, ntt_stream_t stream);
 
 /* Capture ntt_batch_exec into a CUDA graph once (first call) and replay it on
