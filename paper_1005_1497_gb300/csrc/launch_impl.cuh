@@ -202,8 +202,8 @@ static cudaError_t launch_cols_inv(const ColArgs<W> &a, cudaStream_t st)
             k_cols_mid_inv<W, L, CS::LR, CS::LB, TW><<<(int)((t2 + 255) / 256), 256, 0, st>>>(a);
         }
         const long long threads = a.npairs << CS::TOPLR;
-        if constexpr (DST == 0 && sizeof(W) == 4 && L - CS::TOPLR == 5)
-            k_cols_inv5<W, L, CS::TOPLR, TW && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
+        if constexpr (sizeof(W) == 4 && L - CS::TOPLR == 5)
+            k_cols_inv5<W, L, CS::TOPLR, DST, TW && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         else
             k_cols_inv<W, L, CS::TOPLR, DST, TW && !CS::TWO><<<(int)((threads + 255) / 256), 256, 0, st>>>(a);
         return launched(CS::TWO ? 2 : 1);

@@ -927,14 +927,16 @@ __global__ void __launch_bounds__(256) k_cols_inv(const __grid_constant__ ColArg
 }
 
 // The same with at most 48 registers, five blocks per SM for the loads in
-// flight: used for 32-bit words with contiguous output and five column bits,
-// where the plain bound takes 56 registers (four blocks); measured 1.7%
-// faster for 64 x 2^19 on GB300.  (An explicit bound raises the register
-// count of the shorter and 64-bit forms instead, so they keep the plain one.)
-template <typename W, int L, int LR, bool TWIST>
+// flight: used for 32-bit words with five column bits, where the plain bound
+// takes 56 registers with contiguous output and 58 with descriptor output
+// (four blocks); measured on GB300 1.7% faster for 64 x 2^19 (contiguous)
+// and 12-14% faster for 714 x 2^19 (descriptors).  (An explicit bound raises
+// the register count of the shorter and 64-bit forms instead, so they keep
+// the plain one.)
+template <typename W, int L, int LR, int DST, bool TWIST>
 __global__ void __launch_bounds__(256, 5) k_cols_inv5(const __grid_constant__ ColArgs<W> a)
 {
-    cols_inv_body<W, L, LR, 0, TWIST>(a);
+    cols_inv_body<W, L, LR, DST, TWIST>(a);
 }
 
 // Split path with more column bits than one thread holds (L - LR > 5):

@@ -276,7 +276,7 @@ int main(int argc, char **argv)
     ColArgs<uint32_t> plain{f, g, nullptr, s0, s1, h0, np, 0, dtw, c, nullptr, nullptr, dpd};
     const int grid = (int)(((np << LR) + 255) / 256);
     auto fwd = [&] { k_cols_fwd<uint32_t, L, LR, 2, 0, true><<<grid, 256>>>(plain); };
-    auto inv = [&] { k_cols_inv5<uint32_t, L, LR, true><<<grid, 256>>>(plain); };
+    auto inv = [&] { k_cols_inv5<uint32_t, L, LR, 0, true><<<grid, 256>>>(plain); };
     fwd(); inv();
     CK(cudaDeviceSynchronize());
     printf("plain_fwd 256 - %.4f 0 0\n", time_ms(fwd, reps));
