@@ -55,7 +55,7 @@ struct BatchClass {
     size_t count = 0;
     void *scratch = nullptr;         // split path: owned by the batch plan
     uint32_t wave = 0;
-    double work = 0;                 // N log N count, for stream assignment
+    double work = 0;                 // N log N count: classes launch largest work first
     int stream = 0;
 };
 
