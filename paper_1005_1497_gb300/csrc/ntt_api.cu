@@ -537,9 +537,23 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
     }
     const unsigned char *fb = (const unsigned char *)f, *gb = (const unsigned char *)g;
     unsigned char *hb = (unsigned char *)h;
-    size_t i = 0;
-    for (size_t b0 = ndirect; b0 < batch; b0 += chunk, ++i) {
-        const size_t nb = std::min(chunk, batch - b0);
+    // Chunk sizes: full chunks, then 1/2, 1/4 and 1/8 of one at the end, so
+    // that the convolution and outbound copy still to run after the last
+    // inbound copy are short (batches of at least four full chunks).
+    std::vector<size_t> sizes;
+    {
+        size_t rem = batch - ndirect, tail = 0;
+        if (chunk >= 8 && rem >= 4 * chunk) tail = chunk / 2 + chunk / 4 + chunk / 8;
+        for (size_t body = rem - tail; body > 0;) {
+            const size_t c = std::min(chunk, body);
+            sizes.push_back(c);
+            body -= c;
+        }
+        if (tail) sizes.insert(sizes.end(), {chunk / 2, chunk / 4, chunk / 8});
+    }
+    size_t b0 = ndirect;
+    for (size_t i = 0; i < sizes.size(); b0 += sizes[i], ++i) {
+        const size_t nb = sizes[i];
         const size_t slot = i % SLOTS;
         unsigned char *base = (unsigned char *)p->stage + slot * 3 * chunk * seq;
         void *df = base, *dg = base + chunk * seq, *dh = base + 2 * chunk * seq;
