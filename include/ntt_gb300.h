@@ -162,10 +162,10 @@ ntt_status conv_circular_plain(ntt_plan_t plan, const void *f_dev, const void *g
 
 /* conv_circular with the inputs and output in HOST memory (pageable or
  * page-locked).  The library copies f and g to the device, convolves and
- * copies h back in chunks of about 32 MB of input, ordered after `stream`'s
+ * copies h back in chunks of 32-48 MB of input, ordered after `stream`'s
  * earlier work, on three internal streams (inbound copies, convolutions,
  * outbound copies) so that those steps of different chunks overlap.  Device
- * staging memory (4 slots x 3 chunks, about 200 MB at most) is allocated on
+ * staging memory (4 slots x 3 chunks, about 300 MB at most) is allocated on
  * first use and kept by the plan.  With page-locked buffers (cudaHostAlloc /
  * cudaHostRegister), which the GPU can address over the C2C link, and
  * whole-sequence lengths, a batch whose f, g and h total at most 96 MB is

@@ -502,15 +502,17 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
         CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "conv_circular_host: sync");
         return NTT_OK;
     }
-    // Chunks of ~32 MB of input (at least one pair) through SLOTS staging
-    // slots, with one stream per engine: every inbound copy on one stream
-    // (the busier direction of the link never waits for a convolution), the
-    // convolutions on a second, the outbound copies on a third; events order
-    // a chunk's steps and free its slot for the chunk SLOTS later.  (Measured
-    // on GB300 over C2C: about 210 GB/s in and 190 GB/s out alone, more with
-    // both directions at once; one copy/compute stream per slot was slower.)
+    // Chunks of ~48 MB of input (~32 MB on the split path; at least one pair)
+    // through SLOTS staging slots, with one stream per engine: every inbound
+    // copy on one stream (the busier direction of the link never waits for a
+    // convolution), the convolutions on a second, the outbound copies on a
+    // third; events order a chunk's steps and free its slot for the chunk
+    // SLOTS later.  (Measured on GB300 over C2C: about 210 GB/s in and 190 GB/s
+    // out alone, more with both directions at once; one copy/compute stream
+    // per slot was slower; 4096 x 2^14 with the shrinking last chunks below:
+    // 24 / 32 / 48 / 64 MB chunks 3.16 / 3.09 / 3.03 / 3.02-3.05 ms.)
     constexpr int SLOTS = 4;
-    size_t chunk = std::max<size_t>(1, (size_t)(32u << 20) / (2 * seq));
+    size_t chunk = std::max<size_t>(1, (size_t)(p->split ? 32u << 20 : 48u << 20) / (2 * seq));
     chunk = std::min(chunk, batch);
     if (!p->stage || p->stage_pairs < chunk) {
         cudaFree(p->stage);
@@ -539,11 +541,14 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
     unsigned char *hb = (unsigned char *)h;
     // Chunk sizes: full chunks, then 1/2, 1/4 and 1/8 of one at the end, so
     // that the convolution and outbound copy still to run after the last
-    // inbound copy are short (batches of at least four full chunks).
+    // inbound copy are short (whole-sequence lengths, batches of at least four
+    // full chunks).  The split path keeps full chunks: a few pairs of 2^19 are
+    // too few rows for the GPU (64 x 2^19 end to end 1.65 -> 2.13 ms with the
+    // shrinking chunks).
     std::vector<size_t> sizes;
     {
         size_t rem = batch - ndirect, tail = 0;
-        if (chunk >= 8 && rem >= 4 * chunk) tail = chunk / 2 + chunk / 4 + chunk / 8;
+        if (!p->split && chunk >= 8 && rem >= 4 * chunk) tail = chunk / 2 + chunk / 4 + chunk / 8;
         for (size_t body = rem - tail; body > 0;) {
             const size_t c = std::min(chunk, body);
             sizes.push_back(c);

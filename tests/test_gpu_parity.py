@@ -347,11 +347,12 @@ def test_host_buffers_default_choice(ntt, orc, monkeypatch):
 
 
 def test_host_buffers_many_chunks(ntt, orc):
-    """More chunks than the host pipeline has slots (1100 pairs of 2^14:
-    four full chunks of 256 pairs and a ragged fifth), so slots are reused
-    within a call; identical to the device path, and the last pairs checked
-    against Eq. 1 on sampled outputs."""
-    N, batch = 1 << 14, 1100
+    """More chunks than the host pipeline has slots (2000 pairs of 2^14:
+    four full chunks of 384 pairs, a ragged fifth and the three shrinking
+    last chunks), so slots are reused within a call; identical to the device
+    path, and pairs on the chunk borders checked against Eq. 1 on sampled
+    outputs."""
+    N, batch = 1 << 14, 2000
     plan = ntt.Plan(M, N)
     ft = inputs.uniform_mod_torch(M, batch * N, 77, 0, device="cpu").view(batch, N).pin_memory()
     gt = inputs.uniform_mod_torch(M, batch * N, 77, 1, device="cpu").view(batch, N).pin_memory()
@@ -361,7 +362,7 @@ def test_host_buffers_many_chunks(ntt, orc):
     want = ntt.conv_circular(plan, ft.cuda(), gt.cuda()).cpu()
     assert torch.equal(ht, want)
     rng = np.random.default_rng(5)
-    for b in (0, 255, 256, 1023, 1024, batch - 1):
+    for b in (0, 383, 384, 1535, 1536, 1663, 1664, 1856, 1952, batch - 1):
         idx = rng.integers(0, N, 16, dtype=np.uint64)
         fb, gb = ft[b].numpy().astype(np.uint64), gt[b].numpy().astype(np.uint64)
         got = ht[b].numpy().astype(np.uint64)[idx.astype(np.int64)]
