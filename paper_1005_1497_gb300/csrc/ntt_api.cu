@@ -17,6 +17,7 @@
 #include "../../include/ntt_gb300.h"
 #include "ntt_launch.h"
 #include "nt_host.h"
+#include "host_sched.h"
 #include "ntt_internal.h"
 
 using ntt::ColArgs;
@@ -121,20 +122,6 @@ static void fill_modc(ModC<W> &c, uint64_t m, uint64_t ninv)
     c.ninvp = (W)nt::shoup_quot(ninv, m, B);
 }
 
-// Largest batch of a one-warp length (L <= RB + 5) that conv_circular runs
-// with one block per pair (k_conv_small) instead of one warp per pair.  The
-// one-warp kernels win once the batch fills the GPU: measured on GB300, the
-// crossover lies near 16 KB of input per SM (2^10, 32-bit words: 608 pairs;
-// 64-bit words at 2^9: between 608 and 1216), and beyond 32 pairs per SM the
-// block-per-pair kernel's idle threads at the shortest lengths cost more.
-static long long small_batch_max(int word, int L, int nsm)
-{
-    const int rw = word == 32 ? ntt::Arith<uint32_t>::RB + 5 : ntt::Arith<uint64_t>::RB + 5;
-    if (L > rw) return 0;
-    const long long by_bytes = (long long)nsm * 16384 / ((1LL << L) * (word / 8));
-    return std::max<long long>(1, std::min<long long>(by_bytes, (long long)nsm * 32));
-}
-
 static int num_sms()
 {
     int dev = 0, n = 1;
@@ -186,7 +173,9 @@ extern "C" ntt_status ntt_plan(uint64_t m, uint32_t N, ntt_plan_t *out)
     p->split = L > lrmax;
     p->LR = p->split ? lrmax : L;
     if (!p->split) p->block = ntt_default_block(word, L);
-    if (!p->split) p->small_max = small_batch_max(word, L, p->nsm);
+    if (!p->split)                                      // one block per pair below this batch (host_sched.h)
+        p->small_max = ntt::small_batch_max(L, (word == 32 ? ntt::Arith<uint32_t>::RB : ntt::Arith<uint64_t>::RB) + 5,
+                                            word / 8, p->nsm);
     ntt_schedule_t sched;
     const bool tuned = ntt_tuned_schedule(word, L, &sched);
     if (!p->split && tuned) {
@@ -502,7 +491,7 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
         CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "conv_circular_host: sync");
         return NTT_OK;
     }
-    // Chunks of ~48 MB of input (~32 MB on the split path; at least one pair)
+    // Chunks of ~48 MB of input (~32 MB on the split path; host_sched.h)
     // through SLOTS staging slots, with one stream per engine: every inbound
     // copy on one stream (the busier direction of the link never waits for a
     // convolution), the convolutions on a second, the outbound copies on a
@@ -512,8 +501,7 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
     // per slot was slower; 4096 x 2^14 with the shrinking last chunks below:
     // 24 / 32 / 48 / 64 MB chunks 3.16 / 3.09 / 3.03 / 3.02-3.05 ms.)
     constexpr int SLOTS = 4;
-    size_t chunk = std::max<size_t>(1, (size_t)(p->split ? 32u << 20 : 48u << 20) / (2 * seq));
-    chunk = std::min(chunk, batch);
+    size_t chunk = ntt::host_chunk_pairs(seq, p->split, batch);
     if (!p->stage || p->stage_pairs < chunk) {
         cudaFree(p->stage);
         p->stage = nullptr;
@@ -539,23 +527,10 @@ extern "C" ntt_status conv_circular_host(ntt_plan_t p, const void *f, const void
     }
     const unsigned char *fb = (const unsigned char *)f, *gb = (const unsigned char *)g;
     unsigned char *hb = (unsigned char *)h;
-    // Chunk sizes: full chunks, then 1/2, 1/4 and 1/8 of one at the end, so
-    // that the convolution and outbound copy still to run after the last
-    // inbound copy are short (whole-sequence lengths, batches of at least four
-    // full chunks).  The split path keeps full chunks: a few pairs of 2^19 are
-    // too few rows for the GPU (64 x 2^19 end to end 1.65 -> 2.13 ms with the
-    // shrinking chunks).
-    std::vector<size_t> sizes;
-    {
-        size_t rem = batch - ndirect, tail = 0;
-        if (!p->split && chunk >= 8 && rem >= 4 * chunk) tail = chunk / 2 + chunk / 4 + chunk / 8;
-        for (size_t body = rem - tail; body > 0;) {
-            const size_t c = std::min(chunk, body);
-            sizes.push_back(c);
-            body -= c;
-        }
-        if (tail) sizes.insert(sizes.end(), {chunk / 2, chunk / 4, chunk / 8});
-    }
+    // Chunk sizes: the last ones shrink for whole-sequence lengths.  The split
+    // path keeps full chunks: a few pairs of 2^19 are too few rows for the GPU
+    // (64 x 2^19 end to end 1.65 -> 2.13 ms with the shrinking chunks).
+    const std::vector<size_t> sizes = ntt::host_chunk_sizes(batch - ndirect, chunk, !p->split);
     size_t b0 = ndirect;
     for (size_t i = 0; i < sizes.size(); b0 += sizes[i], ++i) {
         const size_t nb = sizes[i];
