@@ -157,3 +157,35 @@ def test_schedule_file_roundtrip_without_a_gpu(ntt, tmp_path):
         bad = tmp_path / "bad.json"
         bad.write_text('{"schedules": []}\n')
         ntt.ntt_autotune_load(str(bad))
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has, in the C header compiled as plain
+    C, the same size and the same offset for every field as its ctypes twin
+    (a stale mirror would hand the library shifted fields)."""
+    import shutil
+    import subprocess
+
+    from paper_1005_1497_gb300 import ntt as mod
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = [("ntt_plan_info_t", mod.PlanInfo), ("ntt_exact_info_t", mod.ExactInfo), ("ntt_conv_desc", mod.ConvDesc),
+             ("ntt_server_config", mod.ServerConfig), ("ntt_server_stats", mod.ServerStats),
+             ("ntt_tune_result", mod.TuneResult)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ntt_gb300.h"', "int main(void) {"]
+    want = []
+    for cname, py in pairs:
+        lines.append(f'    printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append(getattr(py, fname).offset)
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe])
+    got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
